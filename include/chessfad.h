@@ -1,0 +1,177 @@
+/*
+ * chessfad.h -- C ABI of the GB300 (sm_103a) chunked-hDual Hessian /
+ * Hessian-vector-product library.
+ *
+ * The method is CHESSFAD (Ranjan & Zubair, arXiv:2410.22575): forward-mode
+ * AD on "hDual" numbers that carry a value, the derivative with respect to
+ * the Hessian row variable x_i, the derivatives with respect to a contiguous
+ * chunk of csize variables, and the csize second derivatives
+ * d2f/dx_i dx_{cstart+l} (Sec. III-B, Sec. IV / Fig. 1).  One evaluation of f
+ * on seeded hDuals (CHUNK-INIT, Alg. 4) yields one chunk of one Hessian row;
+ * n * ceil(n/csize) evaluations give the whole Hessian (CHUNK-HESS, Alg. 5),
+ * and each chunk, dotted with the matching slice of v and summed over the
+ * row, gives (H v)_i (CHESS-VEC, Alg. 7; Sec. III-C).  The library evaluates
+ * this at many independent points at once, the paper's L0/L1/L2 parallelism
+ * over (point, row, chunk) (Sec. VI, Alg. 9, Alg. 10, Fig. 2).
+ *
+ * Conventions for every call below:
+ *  - Pointers named "device" must point to device memory of the current
+ *    device; the caller owns every buffer.  The compute calls allocate no
+ *    memory, never synchronise the host, and are ordered on `stream`
+ *    (NULL = the legacy default stream).
+ *  - Layout is point-major and row-major: x, v, out are [batch][n]; a
+ *    Hessian is [batch][n][n].  Outputs are overwritten, never accumulated.
+ *  - Precision CHESSFAD_FP64: x, v, out, H are double and all arithmetic is
+ *    FP64.  CHESSFAD_FP32_COMP: x, v, out, H are float; the hDual arithmetic
+ *    runs in FP32 with FMA, the row-times-v products and the reductions over
+ *    a function's terms use error-free transformations (TwoProd by FMA,
+ *    TwoSum), and the sums whose cancellation matters -- the Fletcher-Powell
+ *    residuals E_m - sum_j(...) and the Ackley sums under sqrt and exp -- are
+ *    computed in FP64 once per point.  Fletcher-Powell A, B, E are always
+ *    double.
+ *  - csize (the chunk size) must be one of 1, 2, 4, 8, 16, 32, or 0 for
+ *    "choose for me" (the autotuned table entry for (function, n, precision)
+ *    if one exists, else a default).  It need not divide n: the last chunk is
+ *    ragged and its positions beyond n are never seeded.
+ *  - 1 <= n <= CHESSFAD_MAX_N.  batch == 0 is a valid no-op; batch < 0 is an
+ *    error.  NaN and Inf inputs propagate; they are not trapped.  The
+ *    Ackley Hessian is undefined where sum x_k^2 == 0 (sqrt at 0); the
+ *    library returns whatever the hDual sqrt rule gives there (Inf/NaN).
+ *  - Return value: CHESSFAD_SUCCESS (0) or a negative CHESSFAD_ERR_* code;
+ *    chessfad_strerror() names it.  Argument errors are detected on the host
+ *    before anything is launched.  CHESSFAD_ERR_CUDA reports a launch or
+ *    runtime error taken from the CUDA runtime.
+ */
+#ifndef CHESSFAD_H
+#define CHESSFAD_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define CHESSFAD_API __attribute__((visibility("default")))
+#else
+#define CHESSFAD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is `struct CUstream_st *` */
+typedef struct CUstream_st *chessfad_stream_t;
+
+/* Test functions (named in Sec. VII of the paper). */
+#define CHESSFAD_ROSENBROCK 0      /* f = sum_{k<n-1} 100(x_{k+1}-x_k^2)^2 + (1-x_k)^2 */
+#define CHESSFAD_ACKLEY 1          /* f = -20 exp(-0.2 sqrt(sum x^2/n)) - exp(sum cos(2 pi x)/n) + 20 + e */
+#define CHESSFAD_FLETCHER_POWELL 2 /* f = sum_m (E_m - sum_j (A_mj sin x_j + B_mj cos x_j))^2 */
+
+/* Precisions. */
+#define CHESSFAD_FP64 0
+#define CHESSFAD_FP32_COMP 1
+
+#define CHESSFAD_MAX_N 512
+
+/* Status codes. */
+#define CHESSFAD_SUCCESS 0
+#define CHESSFAD_ERR_FUNCTION (-1)  /* unknown function id */
+#define CHESSFAD_ERR_SIZE (-2)      /* n < 1 or n > CHESSFAD_MAX_N */
+#define CHESSFAD_ERR_BATCH (-3)     /* batch < 0 */
+#define CHESSFAD_ERR_CHUNK (-4)     /* csize not in {0,1,2,4,8,16,32} */
+#define CHESSFAD_ERR_NULL (-5)      /* a required pointer is NULL */
+#define CHESSFAD_ERR_PARAMS (-6)    /* Fletcher-Powell parameters missing or ld < n */
+#define CHESSFAD_ERR_PRECISION (-7) /* unknown precision */
+#define CHESSFAD_ERR_WORKSPACE (-8) /* workspace missing or too small */
+#define CHESSFAD_ERR_CONFIG (-9)    /* launch configuration out of range */
+#define CHESSFAD_ERR_CUDA (-10)     /* CUDA runtime / launch error */
+#define CHESSFAD_ERR_PLAN (-11)     /* ragged plan invalid or built for another precision */
+
+/* Fletcher-Powell parameters, shared by the whole batch.  A, B: device,
+ * double, row-major with leading dimension ld >= n; the leading n x n block
+ * is used.  E: device, double, n entries.  Passed by host pointer. */
+typedef struct {
+    const double *A;
+    const double *B;
+    const double *E;
+    int ld;
+} chessfad_fp_params;
+
+/* Launch configuration of the (point, row, chunk) decomposition.
+ *   csize            chunk size, 1..32 power of two
+ *   threads_per_row  lanes sharing one Hessian row (power of two, 1..32);
+ *                    lane r of a row evaluates chunks r, r+tpr, ... and the
+ *                    row sum is finished by warp shuffles (Sec. VI, Fig. 2
+ *                    does this through shared memory)
+ *   block_threads    CTA size, multiple of 32, 32..256
+ * Zero in any field means "default". */
+typedef struct {
+    int csize;
+    int threads_per_row;
+    int block_threads;
+} chessfad_config;
+
+/* out[p][i] = sum_j H(x_p)[i][j] v[p][j] for p < batch (CHESS-VEC, Alg. 7,
+ * evaluated per point with the L2 decomposition of Sec. VI).
+ *   fn      CHESSFAD_ROSENBROCK / _ACKLEY / _FLETCHER_POWELL
+ *   n       number of variables
+ *   batch   number of points
+ *   csize   chunk size (see conventions), 0 = tuned/default
+ *   x, v    device, [batch][n], double (FP64) or float (FP32_COMP)
+ *   out     device, [batch][n], same type; must not overlap x or v
+ *   params  host pointer to device Fletcher-Powell parameters; required for
+ *           CHESSFAD_FLETCHER_POWELL, ignored otherwise
+ *   prec    CHESSFAD_FP64 or CHESSFAD_FP32_COMP
+ *   stream  CUDA stream */
+CHESSFAD_API int chessfad_hvp(int fn, int n, long long batch, int csize, const void *x, const void *v, void *out,
+                 const chessfad_fp_params *params, int prec, chessfad_stream_t stream);
+
+/* H[p][i][j] = d2f/dx_i dx_j at x_p, both triangles, every entry computed
+ * (CHUNK-HESS, Alg. 5).  H: device, [batch][n][n], double or float by prec;
+ * other arguments as chessfad_hvp. */
+CHESSFAD_API int chessfad_hessian(int fn, int n, long long batch, int csize, const void *x, void *H,
+                     const chessfad_fp_params *params, int prec, chessfad_stream_t stream);
+
+/* As chessfad_hvp / chessfad_hessian with an explicit launch configuration
+ * (cfg may be NULL = defaults). */
+CHESSFAD_API int chessfad_hvp_config(int fn, int n, long long batch, const chessfad_config *cfg, const void *x,
+                        const void *v, void *out, const chessfad_fp_params *params, int prec,
+                        chessfad_stream_t stream);
+CHESSFAD_API int chessfad_hessian_config(int fn, int n, long long batch, const chessfad_config *cfg, const void *x,
+                            void *H, const chessfad_fp_params *params, int prec, chessfad_stream_t stream);
+
+/* The configuration chessfad_hvp would use for csize = 0 (tuned entry if
+ * present, else the default).  Host only; launches nothing. */
+CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg);
+
+/* Autotune the HVP launch configuration for (fn, n, prec) by timing the
+ * candidate (csize, threads_per_row, block_threads) triples on the caller's
+ * buffers (x, v, out as for chessfad_hvp; out is overwritten), starting from
+ * the Sec. V operation-count model and discarding candidates whose kernels
+ * spill registers.  The winner is stored in the process-wide table used by
+ * csize = 0 and returned in *best (may be NULL).  Synchronises `stream`.
+ * Allocates no device memory. */
+CHESSFAD_API int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,
+                          const chessfad_fp_params *params, int prec, chessfad_stream_t stream,
+                          chessfad_config *best);
+
+/* Peak CUDA-core throughput measured on the current device by a dependent-
+ * chain FMA microbenchmark over all SMs: FP32 FFMA for CHESSFAD_FP32_COMP,
+ * FP64 DFMA for CHESSFAD_FP64, counting one FMA as two flops.  Synchronises
+ * the device; allocates no device memory. */
+CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s);
+
+/* Registers per thread and local-memory (spill) bytes per thread of the
+ * HVP (hvp != 0) or Hessian kernel for (fn, prec, csize), as compiled for
+ * the current device.  Host only; launches nothing. */
+CHESSFAD_API int chessfad_kernel_info(int fn, int prec, int csize, int hvp, int *registers, long long *local_bytes);
+
+/* Human-readable name of a status code (static storage). */
+CHESSFAD_API const char *chessfad_strerror(int status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+CHESSFAD_API int chessfad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHESSFAD_H */

@@ -1,0 +1,218 @@
+"""GB300-native chunked-hDual Hessian / Hessian-vector-product library.
+
+A thin ctypes binding over ``_build/libchessfad.so`` (see ``include/chessfad.h``
+for the C ABI).  The functions named ``chessfad_*`` have the C names and take
+the C arguments; device buffers may be passed as ``torch`` CUDA tensors (their
+``data_ptr()`` is used) or as raw integer addresses, streams as
+``torch.cuda.Stream`` or raw handles.  PyTorch is only the allocator and stream
+provider: every step of the hot path runs in the library's CUDA kernels.  There
+is no CPU fallback -- if the library is missing or fails to load, every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+ROSENBROCK, ACKLEY, FLETCHER_POWELL = 0, 1, 2
+FP64, FP32_COMP = 0, 1
+MAX_N = 512
+
+SUCCESS = 0
+ERR = {
+    -1: "FUNCTION", -2: "SIZE", -3: "BATCH", -4: "CHUNK", -5: "NULL", -6: "PARAMS",
+    -7: "PRECISION", -8: "WORKSPACE", -9: "CONFIG", -10: "CUDA", -11: "PLAN",
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ChessfadError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})" if what else f"{strerror(status)} ({status})")
+
+
+class FPParams(ctypes.Structure):
+    """chessfad_fp_params: device pointers to A, B (row-major, leading dim ld) and E."""
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("E", ctypes.c_void_p), ("ld", ctypes.c_int)]
+
+
+class Config(ctypes.Structure):
+    """chessfad_config: chunk size, threads per row, CTA size (0 = default)."""
+    _fields_ = [("csize", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("block_threads", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"csize": self.csize, "threads_per_row": self.threads_per_row, "block_threads": self.block_threads}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libchessfad not built ({_build.LIB}); run python -m paper_2410_22575_gb300.build")
+        lib = ctypes.CDLL(_build.LIB)
+        P, I, L = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+        lib.chessfad_hvp.argtypes = [I, I, L, I, P, P, P, P, I, P]
+        lib.chessfad_hessian.argtypes = [I, I, L, I, P, P, P, I, P]
+        lib.chessfad_hvp_config.argtypes = [I, I, L, P, P, P, P, P, I, P]
+        lib.chessfad_hessian_config.argtypes = [I, I, L, P, P, P, P, I, P]
+        lib.chessfad_default_config.argtypes = [I, I, L, I, P]
+        lib.chessfad_autotune_hvp.argtypes = [I, I, L, P, P, P, P, I, P, P]
+        lib.chessfad_peak_flops.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+        lib.chessfad_kernel_info.argtypes = [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(L)]
+        lib.chessfad_strerror.argtypes = [I]
+        lib.chessfad_strerror.restype = ctypes.c_char_p
+        lib.chessfad_version.argtypes = []
+        for name in ("chessfad_hvp", "chessfad_hessian", "chessfad_hvp_config", "chessfad_hessian_config",
+                     "chessfad_default_config", "chessfad_autotune_hvp", "chessfad_peak_flops",
+                     "chessfad_kernel_info", "chessfad_version"):
+            getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def _addr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    raise TypeError(f"expected a device tensor or an address, got {type(t)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def fp_params(A, B, E) -> FPParams:
+    """FPParams from device tensors (float64, A/B row-major [*, ld])."""
+    return FPParams(_addr(A), _addr(B), _addr(E), int(A.shape[1]))
+
+
+def _check(status: int, what: str) -> int:
+    if status != SUCCESS:
+        raise ChessfadError(status, what)
+    return status
+
+
+def strerror(status: int) -> str:
+    return load().chessfad_strerror(status).decode()
+
+
+# ------------------------------------------------------------ C-named calls
+def chessfad_hvp(fn, n, batch, csize, x, v, out, params=None, prec=FP64, stream=None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    return load().chessfad_hvp(fn, n, batch, csize, _addr(x), _addr(v), _addr(out), p, prec, _stream(stream))
+
+
+def chessfad_hessian(fn, n, batch, csize, x, H, params=None, prec=FP64, stream=None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    return load().chessfad_hessian(fn, n, batch, csize, _addr(x), _addr(H), p, prec, _stream(stream))
+
+
+def chessfad_hvp_config(fn, n, batch, cfg, x, v, out, params=None, prec=FP64, stream=None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    c = ctypes.byref(cfg) if cfg is not None else None
+    return load().chessfad_hvp_config(fn, n, batch, c, _addr(x), _addr(v), _addr(out), p, prec, _stream(stream))
+
+
+def chessfad_hessian_config(fn, n, batch, cfg, x, H, params=None, prec=FP64, stream=None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    c = ctypes.byref(cfg) if cfg is not None else None
+    return load().chessfad_hessian_config(fn, n, batch, c, _addr(x), _addr(H), p, prec, _stream(stream))
+
+
+def chessfad_default_config(fn, n, batch, prec) -> Config:
+    cfg = Config()
+    _check(load().chessfad_default_config(fn, n, batch, prec, ctypes.byref(cfg)), "chessfad_default_config")
+    return cfg
+
+
+def chessfad_autotune_hvp(fn, n, batch, x, v, out, params=None, prec=FP64, stream=None) -> Config:
+    cfg = Config()
+    p = ctypes.byref(params) if params is not None else None
+    _check(load().chessfad_autotune_hvp(fn, n, batch, _addr(x), _addr(v), _addr(out), p, prec, _stream(stream),
+                                        ctypes.byref(cfg)), "chessfad_autotune_hvp")
+    return cfg
+
+
+def chessfad_peak_flops(prec) -> float:
+    f = ctypes.c_double()
+    _check(load().chessfad_peak_flops(prec, ctypes.byref(f)), "chessfad_peak_flops")
+    return f.value
+
+
+def chessfad_kernel_info(fn, prec, csize, hvp=True) -> dict:
+    regs = ctypes.c_int()
+    local = ctypes.c_longlong()
+    _check(load().chessfad_kernel_info(fn, prec, csize, int(bool(hvp)), ctypes.byref(regs), ctypes.byref(local)),
+           "chessfad_kernel_info")
+    return {"registers": regs.value, "local_bytes": local.value}
+
+
+def chessfad_strerror(status) -> str:
+    return strerror(status)
+
+
+def chessfad_version() -> int:
+    return load().chessfad_version()
+
+
+# ------------------------------------------------------------ conveniences
+def _dtype(prec):
+    import torch
+
+    return torch.float64 if prec == FP64 else torch.float32
+
+
+def hvp(fn, x, v, csize=0, params=None, prec=None, stream=None, out=None, cfg=None):
+    """out = H(x_p) v_p for device tensors x, v of shape [batch, n]."""
+    import torch
+
+    if prec is None:
+        prec = FP64 if x.dtype == torch.float64 else FP32_COMP
+    batch, n = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    if cfg is not None:
+        _check(chessfad_hvp_config(fn, n, batch, cfg, x, v, out, params, prec, stream), "chessfad_hvp_config")
+    else:
+        _check(chessfad_hvp(fn, n, batch, csize, x, v, out, params, prec, stream), "chessfad_hvp")
+    return out
+
+
+def hessian(fn, x, csize=0, params=None, prec=None, stream=None, out=None, cfg=None):
+    """H[p] = Hessian of f at x_p for a device tensor x of shape [batch, n]."""
+    import torch
+
+    if prec is None:
+        prec = FP64 if x.dtype == torch.float64 else FP32_COMP
+    batch, n = x.shape
+    if out is None:
+        out = torch.empty((batch, n, n), dtype=x.dtype, device=x.device)
+    if cfg is not None:
+        _check(chessfad_hessian_config(fn, n, batch, cfg, x, out, params, prec, stream), "chessfad_hessian_config")
+    else:
+        _check(chessfad_hessian(fn, n, batch, csize, x, out, params, prec, stream), "chessfad_hessian")
+    return out

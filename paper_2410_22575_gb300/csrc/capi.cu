@@ -1,0 +1,311 @@
+// capi.cu -- the extern "C" boundary of include/chessfad.h: argument checks,
+// launch-configuration choice (defaults, autotuned table), dispatch to the
+// kernel instantiation units, the autotuner and status strings.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "../../include/chessfad.h"
+#include "dispatch.h"
+
+namespace chessfad {
+
+static int next_pow2(int v)
+{
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+static bool valid_chunk(int c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
+
+// Tuned configurations keyed by (fn, n, prec).
+static std::mutex g_mu;
+static std::map<std::tuple<int, int, int>, chessfad_config> g_table;
+
+// Default: the largest chunk that keeps the hDual state comfortably in
+// registers (the plain method's multiplication count (6 + 3/c) n^2 M falls
+// with c, Sec. V), one chunk per lane where a row has <= 32 chunks.
+static chessfad_config default_config(int fn, int n, int prec)
+{
+    chessfad_config c{};
+    int cmax = (prec == CHESSFAD_FP64) ? 8 : 16;
+    if (fn == CHESSFAD_FLETCHER_POWELL) cmax = (prec == CHESSFAD_FP64) ? 4 : 8;
+    c.csize = std::min(cmax, next_pow2(n));
+    const int nch = (n + c.csize - 1) / c.csize;
+    c.threads_per_row = std::min(32, next_pow2(nch));
+    c.block_threads = 256;
+    return c;
+}
+
+static chessfad_config resolve(int fn, int n, int prec, const chessfad_config *cfg, int csize_hint)
+{
+    chessfad_config c{};
+    if (cfg) c = *cfg;
+    if (c.csize == 0 && csize_hint != 0) c.csize = csize_hint;
+    if (c.csize == 0) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_table.find(std::make_tuple(fn, n, prec));
+        chessfad_config base = (it != g_table.end()) ? it->second : default_config(fn, n, prec);
+        if (c.threads_per_row == 0) c.threads_per_row = base.threads_per_row;
+        if (c.block_threads == 0) c.block_threads = base.block_threads;
+        c.csize = base.csize;
+    }
+    const int nch = (n + c.csize - 1) / c.csize;
+    if (c.threads_per_row == 0) c.threads_per_row = std::min(32, next_pow2(nch));
+    if (c.block_threads == 0) c.block_threads = 256;
+    return c;
+}
+
+static int check_common(int fn, int n, long long batch, int prec, const chessfad_fp_params *params)
+{
+    if (fn < 0 || fn > 2) return CHESSFAD_ERR_FUNCTION;
+    if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
+    if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
+    if (batch < 0) return CHESSFAD_ERR_BATCH;
+    if (fn == CHESSFAD_FLETCHER_POWELL) {
+        if (!params || !params->A || !params->B || !params->E || params->ld < n) return CHESSFAD_ERR_PARAMS;
+    }
+    return CHESSFAD_SUCCESS;
+}
+
+static int check_config(const chessfad_config &c)
+{
+    if (!valid_chunk(c.csize)) return CHESSFAD_ERR_CHUNK;
+    const int t = c.threads_per_row;
+    if (t < 1 || t > 32 || (t & (t - 1))) return CHESSFAD_ERR_CONFIG;
+    if (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32) return CHESSFAD_ERR_CONFIG;
+    return CHESSFAD_SUCCESS;
+}
+
+// Rows of A and B staged per shared-memory tile by the Fletcher-Powell sweep:
+// all n rows when they fit in ~64 KiB, else the largest multiple of 8.
+static int fp_tile_rows(int n, int prec)
+{
+    const size_t esz = (prec == CHESSFAD_FP64) ? 8 : 4;
+    const size_t budget = 64 * 1024;
+    int mt = (int)(budget / (2 * (size_t)n * esz));
+    mt = std::max(8, mt / 8 * 8);
+    return std::min(mt, (n + 7) / 8 * 8);
+}
+
+static int launch(int fn, int n, long long batch, const chessfad_config &c, const void *x, const void *v,
+                  void *out, const chessfad_fp_params *params, int prec, bool hvp, cudaStream_t stream)
+{
+    SweepArgs a{};
+    a.x = x;
+    a.v = v;
+    a.out = out;
+    if (fn == CHESSFAD_FLETCHER_POWELL) {
+        a.A = params->A;
+        a.B = params->B;
+        a.E = params->E;
+        a.ld = params->ld;
+    }
+    a.batch = batch;
+    a.n = n;
+    a.nch = (n + c.csize - 1) / c.csize;
+    a.tpr = c.threads_per_row;
+    a.tpp = n * c.threads_per_row;
+    a.maxpts = (int)std::min<long long>(batch, (c.block_threads - 1) / a.tpp + 2);
+    a.mt = (fn == CHESSFAD_FLETCHER_POWELL) ? fp_tile_rows(n, prec) : 8;
+    if (fn == CHESSFAD_FLETCHER_POWELL && a.mt % fp_mb(c.csize) != 0) return CHESSFAD_ERR_CONFIG;
+    cudaError_t e = cudaErrorInvalidValue;
+    const bool f64 = (prec == CHESSFAD_FP64);
+    switch (fn) {
+    case CHESSFAD_ROSENBROCK:
+        e = f64 ? launch_rosenbrock_f64(c.csize, hvp, a, c.block_threads, stream)
+                : launch_rosenbrock_f32c(c.csize, hvp, a, c.block_threads, stream);
+        break;
+    case CHESSFAD_ACKLEY:
+        e = f64 ? launch_ackley_f64(c.csize, hvp, a, c.block_threads, stream)
+                : launch_ackley_f32c(c.csize, hvp, a, c.block_threads, stream);
+        break;
+    case CHESSFAD_FLETCHER_POWELL:
+        e = f64 ? launch_fp_f64(c.csize, hvp, a, c.block_threads, stream)
+                : launch_fp_f32c(c.csize, hvp, a, c.block_threads, stream);
+        break;
+    }
+    return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+}
+
+static cudaError_t kernel_attr(int fn, int prec, int csize, bool hvp, cudaFuncAttributes *fa)
+{
+    const bool f64 = (prec == CHESSFAD_FP64);
+    switch (fn) {
+    case CHESSFAD_ROSENBROCK: return f64 ? attr_rosenbrock_f64(csize, hvp, fa) : attr_rosenbrock_f32c(csize, hvp, fa);
+    case CHESSFAD_ACKLEY: return f64 ? attr_ackley_f64(csize, hvp, fa) : attr_ackley_f32c(csize, hvp, fa);
+    case CHESSFAD_FLETCHER_POWELL: return f64 ? attr_fp_f64(csize, hvp, fa) : attr_fp_f32c(csize, hvp, fa);
+    }
+    return cudaErrorInvalidValue;
+}
+
+static int run(int fn, int n, long long batch, const chessfad_config *cfg, int csize_hint, const void *x,
+               const void *v, void *out, const chessfad_fp_params *params, int prec, bool hvp,
+               cudaStream_t stream)
+{
+    int st = check_common(fn, n, batch, prec, params);
+    if (st) return st;
+    if (csize_hint != 0 && !valid_chunk(csize_hint)) return CHESSFAD_ERR_CHUNK;
+    if (cfg && cfg->csize != 0 && !valid_chunk(cfg->csize)) return CHESSFAD_ERR_CHUNK;
+    const chessfad_config c = resolve(fn, n, prec, cfg, csize_hint);
+    st = check_config(c);
+    if (st) return st;
+    if (batch == 0) return CHESSFAD_SUCCESS;
+    if (!x || !out || (hvp && !v)) return CHESSFAD_ERR_NULL;
+    return launch(fn, n, batch, c, x, v, out, params, prec, hvp, stream);
+}
+
+}  // namespace chessfad
+
+using namespace chessfad;
+
+extern "C" {
+
+int chessfad_hvp(int fn, int n, long long batch, int csize, const void *x, const void *v, void *out,
+                 const chessfad_fp_params *params, int prec, chessfad_stream_t stream)
+{
+    return run(fn, n, batch, nullptr, csize, x, v, out, params, prec, true, (cudaStream_t)stream);
+}
+
+int chessfad_hessian(int fn, int n, long long batch, int csize, const void *x, void *H,
+                     const chessfad_fp_params *params, int prec, chessfad_stream_t stream)
+{
+    return run(fn, n, batch, nullptr, csize, x, nullptr, H, params, prec, false, (cudaStream_t)stream);
+}
+
+int chessfad_hvp_config(int fn, int n, long long batch, const chessfad_config *cfg, const void *x, const void *v,
+                        void *out, const chessfad_fp_params *params, int prec, chessfad_stream_t stream)
+{
+    return run(fn, n, batch, cfg, 0, x, v, out, params, prec, true, (cudaStream_t)stream);
+}
+
+int chessfad_hessian_config(int fn, int n, long long batch, const chessfad_config *cfg, const void *x, void *H,
+                            const chessfad_fp_params *params, int prec, chessfad_stream_t stream)
+{
+    return run(fn, n, batch, cfg, 0, x, nullptr, H, params, prec, false, (cudaStream_t)stream);
+}
+
+int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg)
+{
+    if (!cfg) return CHESSFAD_ERR_NULL;
+    if (fn < 0 || fn > 2) return CHESSFAD_ERR_FUNCTION;
+    if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
+    if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
+    if (batch < 0) return CHESSFAD_ERR_BATCH;
+    *cfg = resolve(fn, n, prec, nullptr, 0);
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,
+                          const chessfad_fp_params *params, int prec, chessfad_stream_t stream_,
+                          chessfad_config *best)
+{
+    cudaStream_t stream = (cudaStream_t)stream_;
+    int st = check_common(fn, n, batch, prec, params);
+    if (st) return st;
+    if (batch == 0) return CHESSFAD_ERR_BATCH;
+    if (!x || !v || !out) return CHESSFAD_ERR_NULL;
+
+    // Candidate chunk sizes: powers of two up to next_pow2(n), ordered by the
+    // Sec. V model of the plain method, whose multiplication count
+    // (6 + 3/c) n^2 M falls with c, so large chunks are tried first.
+    std::vector<int> chunks;
+    for (int c = std::min(32, next_pow2(n)); c >= 1; c >>= 1) chunks.push_back(c);
+
+    // Time on a prefix of the batch big enough to fill the GPU several times.
+    const long long want_threads = 8LL * 152 * 256;
+    long long sub = std::min<long long>(batch, std::max<long long>(1, want_threads / n));
+
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CHESSFAD_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CHESSFAD_ERR_CUDA;
+    }
+    chessfad_config win{};
+    float win_ms = INFINITY;
+    int rc = CHESSFAD_SUCCESS;
+    for (int c : chunks) {
+        cudaFuncAttributes fa{};
+        if (kernel_attr(fn, prec, c, true, &fa) != cudaSuccess || fa.localSizeBytes > 0) continue;  // spills
+        const int nch = (n + c - 1) / c;
+        const int tmax = std::min(32, next_pow2(nch));
+        for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1) {
+            for (int bt : {256, 128}) {
+                chessfad_config cfg{c, t, bt};
+                if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaEventRecord(e0, stream);
+                const int reps = 3;
+                for (int k = 0; k < reps; ++k) launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream);
+                cudaEventRecord(e1, stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = CHESSFAD_ERR_CUDA;
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < win_ms) {
+                    win_ms = ms;
+                    win = cfg;
+                }
+            }
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (!std::isfinite(win_ms)) return CHESSFAD_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_table[std::make_tuple(fn, n, prec)] = win;
+    }
+    if (best) *best = win;
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_kernel_info(int fn, int prec, int csize, int hvp, int *registers, long long *local_bytes)
+{
+    if (!registers || !local_bytes) return CHESSFAD_ERR_NULL;
+    if (fn < 0 || fn > 2) return CHESSFAD_ERR_FUNCTION;
+    if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
+    if (!valid_chunk(csize)) return CHESSFAD_ERR_CHUNK;
+    cudaFuncAttributes fa{};
+    if (kernel_attr(fn, prec, csize, hvp != 0, &fa) != cudaSuccess) return CHESSFAD_ERR_CUDA;
+    *registers = fa.numRegs;
+    *local_bytes = (long long)fa.localSizeBytes;
+    return CHESSFAD_SUCCESS;
+}
+
+const char *chessfad_strerror(int status)
+{
+    switch (status) {
+    case CHESSFAD_SUCCESS: return "success";
+    case CHESSFAD_ERR_FUNCTION: return "unknown function id";
+    case CHESSFAD_ERR_SIZE: return "n out of range [1, CHESSFAD_MAX_N]";
+    case CHESSFAD_ERR_BATCH: return "invalid batch size";
+    case CHESSFAD_ERR_CHUNK: return "chunk size not in {1,2,4,8,16,32} (or 0)";
+    case CHESSFAD_ERR_NULL: return "required pointer is NULL";
+    case CHESSFAD_ERR_PARAMS: return "Fletcher-Powell parameters missing or ld < n";
+    case CHESSFAD_ERR_PRECISION: return "unknown precision";
+    case CHESSFAD_ERR_WORKSPACE: return "workspace missing or too small";
+    case CHESSFAD_ERR_CONFIG: return "launch configuration out of range";
+    case CHESSFAD_ERR_CUDA: return "CUDA runtime or launch error";
+    case CHESSFAD_ERR_PLAN: return "ragged plan invalid or built for another precision";
+    }
+    return "unknown status";
+}
+
+int chessfad_version(void) { return 100; }
+
+}  // extern "C"

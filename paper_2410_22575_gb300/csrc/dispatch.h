@@ -1,0 +1,35 @@
+// dispatch.h -- host-side entry points of the per-(function, precision)
+// kernel instantiation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "sweep.cuh"
+
+namespace chessfad {
+
+// Residual hDuals held in registers at once by the Fletcher-Powell sweep for
+// chunk size C (keeps MB * (2C+1) accumulator registers near 70).
+constexpr int fp_mb(int C) { return C <= 4 ? 8 : 32 / C; }
+
+#define CHESSFAD_DECL(name) \
+    cudaError_t name(int C, bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream)
+CHESSFAD_DECL(launch_rosenbrock_f64);
+CHESSFAD_DECL(launch_rosenbrock_f32c);
+CHESSFAD_DECL(launch_ackley_f64);
+CHESSFAD_DECL(launch_ackley_f32c);
+CHESSFAD_DECL(launch_fp_f64);
+CHESSFAD_DECL(launch_fp_f32c);
+#undef CHESSFAD_DECL
+
+// cudaFuncGetAttributes of the instantiation (registers, local memory).
+#define CHESSFAD_ATTR(name) cudaError_t name(int C, bool hvp, cudaFuncAttributes *fa)
+CHESSFAD_ATTR(attr_rosenbrock_f64);
+CHESSFAD_ATTR(attr_rosenbrock_f32c);
+CHESSFAD_ATTR(attr_ackley_f64);
+CHESSFAD_ATTR(attr_ackley_f32c);
+CHESSFAD_ATTR(attr_fp_f64);
+CHESSFAD_ATTR(attr_fp_f32c);
+#undef CHESSFAD_ATTR
+
+}  // namespace chessfad

@@ -1,0 +1,301 @@
+// hdual.cuh -- register-resident chunked hDual numbers and their rules.
+//
+// An hDual<T, C> is the chunked number of Sec. III-B / Sec. IV (Fig. 1):
+//   v      the value                                   (v[0] in Fig. 1)
+//   d1     d/dx_i, i the Hessian row                   (v[1])
+//   g[l]   d/dx_{cstart+l}, l < C, the chunk           (v[2 .. C+1])
+//   h[l]   d2/dx_i dx_{cstart+l}                       (v[C+2 .. 2C+1])
+// C is a template constant so the 2C+2 components live in registers; every
+// loop over components is fully unrolled.
+//
+// The rules are the ones of Sec. III-A generalised to a chunk, as in Fig. 1:
+//   product   (u w)      = u w
+//             (u w)_k    = u w_k + w u_k                       (first order)
+//             (u w)_{il} = u w_{il} + u_i w_l + w_i u_l + w u_{il}
+//   unary     phi(u)     = phi(u),  phi(u)_k = phi'(u) u_k,
+//             phi(u)_{il} = phi'(u) u_{il} + phi''(u) u_i u_l
+//   sums and products with a scalar act componentwise.
+// The "fused" forms (acc + u*w, acc + s*phi(u)) apply exactly these rules
+// and add the result into an accumulator with FMAs; they reorder rounding,
+// not arithmetic, and they keep the FP32/FP64 pipes on FMA instructions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace chessfad {
+
+template <typename T, int C>
+struct HD {
+    T v, d1;
+    T g[C];
+    T h[C];
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> hzero()
+{
+    HD<T, C> r;
+    r.v = T(0);
+    r.d1 = T(0);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = T(0);
+        r.h[l] = T(0);
+    }
+    return r;
+}
+
+// CHUNK-INIT (Alg. 4) for one variable k, generated on the fly instead of
+// materialising y[n]: <x_k, [k == i], e_{k - cstart} if k is in the chunk, 0>.
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart)
+{
+    HD<T, C> y;
+    y.v = xk;
+    y.d1 = (k == i) ? T(1) : T(0);
+    const int d = k - cstart;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        y.g[l] = (d == l) ? T(1) : T(0);
+        y.h[l] = T(0);
+    }
+    return y;
+}
+
+// u * w (Fig. 1).
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> hmul(const HD<T, C> &a, const HD<T, C> &b)
+{
+    HD<T, C> r;
+    r.v = a.v * b.v;
+    r.d1 = fma_(b.v, a.d1, a.v * b.d1);
+#pragma unroll
+    for (int l = 0; l < C; ++l) r.g[l] = fma_(b.v, a.g[l], a.v * b.g[l]);
+#pragma unroll
+    for (int l = 0; l < C; ++l)
+        r.h[l] = fma_(b.v, a.h[l], fma_(b.d1, a.g[l], fma_(a.d1, b.g[l], a.v * b.h[l])));
+    return r;
+}
+
+// acc + u * w: the product rule, each component's terms added into acc.
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> hfma(const HD<T, C> &a, const HD<T, C> &b, const HD<T, C> &acc)
+{
+    HD<T, C> r;
+    r.v = fma_(a.v, b.v, acc.v);
+    r.d1 = fma_(b.v, a.d1, fma_(a.v, b.d1, acc.d1));
+#pragma unroll
+    for (int l = 0; l < C; ++l) r.g[l] = fma_(b.v, a.g[l], fma_(a.v, b.g[l], acc.g[l]));
+#pragma unroll
+    for (int l = 0; l < C; ++l)
+        r.h[l] = fma_(b.v, a.h[l], fma_(b.d1, a.g[l], fma_(a.d1, b.g[l], fma_(a.v, b.h[l], acc.h[l]))));
+    return r;
+}
+
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> hadd(const HD<T, C> &a, const HD<T, C> &b)
+{
+    HD<T, C> r;
+    r.v = a.v + b.v;
+    r.d1 = a.d1 + b.d1;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = a.g[l] + b.g[l];
+        r.h[l] = a.h[l] + b.h[l];
+    }
+    return r;
+}
+
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> hsub(const HD<T, C> &a, const HD<T, C> &b)
+{
+    HD<T, C> r;
+    r.v = a.v - b.v;
+    r.d1 = a.d1 - b.d1;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = a.g[l] - b.g[l];
+        r.h[l] = a.h[l] - b.h[l];
+    }
+    return r;
+}
+
+// s * u
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> smul(T s, const HD<T, C> &a)
+{
+    HD<T, C> r;
+    r.v = s * a.v;
+    r.d1 = s * a.d1;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = s * a.g[l];
+        r.h[l] = s * a.h[l];
+    }
+    return r;
+}
+
+// s - u
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> rsub(T s, const HD<T, C> &a)
+{
+    HD<T, C> r;
+    r.v = s - a.v;
+    r.d1 = -a.d1;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = -a.g[l];
+        r.h[l] = -a.h[l];
+    }
+    return r;
+}
+
+// phi(u) with phi, phi', phi'' evaluated at u.v by the caller.
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> unary(const HD<T, C> &a, T phi, T dphi, T d2phi)
+{
+    HD<T, C> r;
+    r.v = phi;
+    r.d1 = dphi * a.d1;
+    const T q = d2phi * a.d1;
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        r.g[l] = dphi * a.g[l];
+        r.h[l] = fma_(q, a.g[l], dphi * a.h[l]);
+    }
+    return r;
+}
+
+// acc + s * phi(u): the unary rule scaled by s, added into acc.  The value
+// component is skipped when the caller replaces it (kValue == false).
+template <bool kValue, typename T, int C>
+__device__ __forceinline__ void sfma_unary(HD<T, C> &acc, T s, const HD<T, C> &a, T phi, T dphi, T d2phi)
+{
+    if (kValue) acc.v = fma_(s, phi, acc.v);
+    const T sd = s * dphi;
+    const T q = (s * d2phi) * a.d1;
+    acc.d1 = fma_(sd, a.d1, acc.d1);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        acc.g[l] = fma_(sd, a.g[l], acc.g[l]);
+        acc.h[l] = fma_(sd, a.h[l], fma_(q, a.g[l], acc.h[l]));
+    }
+}
+
+// acc + phi(u) (s = 1 of the above).
+template <bool kValue, typename T, int C>
+__device__ __forceinline__ void add_unary(HD<T, C> &acc, const HD<T, C> &a, T phi, T dphi, T d2phi)
+{
+    if (kValue) acc.v += phi;
+    const T q = d2phi * a.d1;
+    acc.d1 = fma_(dphi, a.d1, acc.d1);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        acc.g[l] = fma_(dphi, a.g[l], acc.g[l]);
+        acc.h[l] = fma_(dphi, a.h[l], fma_(q, a.g[l], acc.h[l]));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Error-free transformations (compensated FP32 path).
+//   TwoSum      Knuth (TAOCP vol. 2): s + e == a + b exactly, no ordering
+//               precondition, 6 additions.
+//   TwoProd     with FMA: p + e == a * b exactly (e = fma(a, b, -p)).
+//   Sum2 / Dot2 Ogita, Rump & Oishi, "Accurate sum and dot product", SIAM J.
+//               Sci. Comput. 26(6), 2005: cascade the rounding errors of a
+//               recursive sum / dot product into a second accumulator and add
+//               it once at the end; the result is as accurate as if computed
+//               in twice the working precision, then rounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// A compensated scalar: s + e is the running sum, e collects the rounding
+// errors (Sum2).
+struct CSum {
+    float s, e;
+};
+
+__device__ __forceinline__ void csum_add(CSum &acc, float x)
+{
+    float t;
+    two_sum(acc.s, x, acc.s, t);
+    acc.e = __fadd_rn(acc.e, t);
+}
+
+// acc += a * b with TwoProd + TwoSum (one Dot2 step).
+__device__ __forceinline__ void cdot_add(CSum &acc, float a, float b)
+{
+    float p, pe, t;
+    two_prod(a, b, p, pe);
+    two_sum(acc.s, p, acc.s, t);
+    acc.e = __fadd_rn(acc.e, __fadd_rn(t, pe));
+}
+
+// Merge two compensated partial sums (used across shuffle lanes).
+__device__ __forceinline__ CSum csum_merge(CSum a, CSum b)
+{
+    CSum r;
+    float t;
+    two_sum(a.s, b.s, r.s, t);
+    r.e = __fadd_rn(__fadd_rn(a.e, b.e), t);
+    return r;
+}
+
+__device__ __forceinline__ float csum_value(const CSum &a) { return __fadd_rn(a.s, a.e); }
+
+// A compensated hDual accumulator: Sum2 applied to each component of a sum
+// over terms.  Components the caller never reads are dead code and vanish.
+template <int C>
+struct CHD {
+    HD<float, C> s, e;
+};
+
+template <int C>
+__device__ __forceinline__ void chd_zero(CHD<C> &a)
+{
+    a.s = hzero<float, C>();
+    a.e = hzero<float, C>();
+}
+
+template <int C>
+__device__ __forceinline__ void chd_add(CHD<C> &a, const HD<float, C> &x)
+{
+    float t;
+    two_sum(a.s.v, x.v, a.s.v, t);
+    a.e.v = __fadd_rn(a.e.v, t);
+    two_sum(a.s.d1, x.d1, a.s.d1, t);
+    a.e.d1 = __fadd_rn(a.e.d1, t);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        two_sum(a.s.g[l], x.g[l], a.s.g[l], t);
+        a.e.g[l] = __fadd_rn(a.e.g[l], t);
+        two_sum(a.s.h[l], x.h[l], a.s.h[l], t);
+        a.e.h[l] = __fadd_rn(a.e.h[l], t);
+    }
+}
+
+template <int C>
+__device__ __forceinline__ HD<float, C> chd_value(const CHD<C> &a)
+{
+    return hadd(a.s, a.e);
+}
+
+}  // namespace chessfad

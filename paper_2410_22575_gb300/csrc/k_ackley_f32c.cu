@@ -1,0 +1,47 @@
+// Kernel instantiations: ackley, float hDual arithmetic (f32c), every chunk size.
+#include "dispatch.h"
+
+namespace chessfad {
+
+template <int C>
+static cudaError_t go(bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
+{
+    constexpr int MB = fp_mb(C);
+    return hvp ? launch_sweep<float, C, FN_ACKLEY, true, MB>(a, bt, s) : launch_sweep<float, C, FN_ACKLEY, false, MB>(a, bt, s);
+}
+
+cudaError_t launch_ackley_f32c(int C, bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
+{
+    switch (C) {
+    case 1: return go<1>(hvp, a, bt, s);
+    case 2: return go<2>(hvp, a, bt, s);
+    case 4: return go<4>(hvp, a, bt, s);
+    case 8: return go<8>(hvp, a, bt, s);
+    case 16: return go<16>(hvp, a, bt, s);
+    case 32: return go<32>(hvp, a, bt, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <int C>
+static cudaError_t at(bool hvp, cudaFuncAttributes *fa)
+{
+    constexpr int MB = fp_mb(C);
+    return hvp ? cudaFuncGetAttributes(fa, sweep_kernel<float, C, FN_ACKLEY, true, MB>)
+               : cudaFuncGetAttributes(fa, sweep_kernel<float, C, FN_ACKLEY, false, MB>);
+}
+
+cudaError_t attr_ackley_f32c(int C, bool hvp, cudaFuncAttributes *fa)
+{
+    switch (C) {
+    case 1: return at<1>(hvp, fa);
+    case 2: return at<2>(hvp, fa);
+    case 4: return at<4>(hvp, fa);
+    case 8: return at<8>(hvp, fa);
+    case 16: return at<16>(hvp, fa);
+    case 32: return at<32>(hvp, fa);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace chessfad

@@ -1,0 +1,466 @@
+// sweep.cuh -- the chunked-hDual sweep kernels (Hessian-vector products and
+// full Hessians at many independent points).
+//
+// Work decomposition (the paper's L0/L1/L2 parallelism, Sec. VI, Alg. 9,
+// Alg. 10, Fig. 2): one thread per (point p, Hessian row i, lane r), with tpr
+// lanes per row; lane r evaluates chunks r, r+tpr, r+2tpr, ... of row i.  An
+// evaluation ("sweep") seeds the n variables with CHUNK-INIT (Alg. 4) on the
+// fly, runs the test function on register-resident hDual<C> numbers and
+// leaves d2f/dx_i dx_{cstart+l}, l < C, in the result's h[] (Alg. 5).  For
+// Hessian-vector products the chunk is dotted with v[cstart..cstart+C)
+// (Alg. 7) and the tpr lanes of a row are summed with warp shuffles, where
+// Fig. 2 goes through shared memory and __syncthreads.
+//
+// Per-block staging: the points a block touches are contiguous in x and v, so
+// the block copies them into shared memory with coalesced loads once, together
+// with per-point tables of value-only quantities that every sweep of the point
+// would otherwise recompute: cos/sin(2 pi x_k) (Ackley), sin/cos x_j and the
+// Fletcher-Powell residuals r_m (FP64), the Ackley sums S = sum x_k^2 and
+// C = sum cos(2 pi x_k) (FP64) with the sqrt/exp values taken at them.  The
+// value component of an hDual is the same in every sweep of a point; only
+// the derivative components depend on (row, chunk).  These FP64 sums are the
+// "FP64 islands" of the compensated-FP32 precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <type_traits>
+
+#include "hdual.cuh"
+
+namespace chessfad {
+
+enum { FN_ROSENBROCK = 0, FN_ACKLEY = 1, FN_FP = 2 };
+
+struct SweepArgs {
+    const void *x;
+    const void *v;
+    void *out;
+    const double *A;
+    const double *B;
+    const double *E;
+    long long batch;
+    int n;
+    int ld;
+    int nch;     // ceil(n / C)
+    int tpr;     // threads per row (power of two <= 32)
+    int tpp;     // threads per point = n * tpr
+    int maxpts;  // points staged per block (upper bound)
+    int mt;      // Fletcher-Powell: rows of A, B per shared-memory tile
+};
+
+// Number of Ackley per-point scalars kept in the table.
+constexpr int kAckScal = 8;
+
+// Shared-memory layout, computed identically on host and device.
+template <typename T>
+struct Smem {
+    size_t xs, vs, t1, t2, sc, res, dsin, dcos, at, bt, total;
+};
+
+__host__ __device__ inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+template <typename T>
+__host__ __device__ inline Smem<T> smem_layout(int fn, bool hvp, int n, int maxpts, int mt)
+{
+    Smem<T> s{};
+    size_t off = 0;
+    const size_t pn = (size_t)maxpts * n;
+    s.xs = off; off = align_up(off + pn * sizeof(T), 16);
+    s.vs = off; if (hvp) off = align_up(off + pn * sizeof(T), 16);
+    s.t1 = s.t2 = s.sc = s.res = s.dsin = s.dcos = s.at = s.bt = off;
+    if (fn == FN_ACKLEY) {
+        s.t1 = off; off = align_up(off + pn * sizeof(T), 16);
+        s.t2 = off; off = align_up(off + pn * sizeof(T), 16);
+        s.sc = off; off = align_up(off + (size_t)maxpts * kAckScal * sizeof(T), 16);
+    } else if (fn == FN_FP) {
+        s.t1 = off; off = align_up(off + pn * sizeof(T), 16);    // sin x_j
+        s.t2 = off; off = align_up(off + pn * sizeof(T), 16);    // cos x_j
+        s.res = off; off = align_up(off + pn * sizeof(T), 16);   // residual r_m (FP64-computed)
+        // The FP64 sin/cos scratch of the prologue and the A/B tiles of the
+        // sweep are never live together: they share one region.
+        const size_t u = off;
+        s.dsin = u;
+        s.dcos = align_up(u + pn * sizeof(double), 16);
+        const size_t end1 = align_up(s.dcos + pn * sizeof(double), 16);
+        s.at = u;                                                   // A tile, [j][m]
+        s.bt = align_up(u + (size_t)n * mt * sizeof(T), 16);       // B tile, [j][m]
+        const size_t end2 = align_up(s.bt + (size_t)n * mt * sizeof(T), 16);
+        off = end1 > end2 ? end1 : end2;
+    }
+    s.total = off;
+    return s;
+}
+
+// ------------------------------------------------------------------ sums
+// Sum over a function's terms.  FP64 (and plain) accumulation adds each term
+// with FMAs; the compensated FP32 form runs Sum2 on every component.
+template <typename T, int C, bool COMP>
+struct TermSum;
+
+template <typename T, int C>
+struct TermSum<T, C, false> {
+    HD<T, C> s;
+    __device__ __forceinline__ void init() { s = hzero<T, C>(); }
+    // += a*b + c*d
+    __device__ __forceinline__ void add_prod2(const HD<T, C> &a, const HD<T, C> &b, const HD<T, C> &c,
+                                              const HD<T, C> &d)
+    {
+        s = hfma(a, b, hfma(c, d, s));
+    }
+    __device__ __forceinline__ void add_prod(const HD<T, C> &a, const HD<T, C> &b) { s = hfma(a, b, s); }
+    __device__ __forceinline__ HD<T, C> value() const { return s; }
+};
+
+template <int C>
+struct TermSum<float, C, true> {
+    CHD<C> s;
+    __device__ __forceinline__ void init() { chd_zero(s); }
+    __device__ __forceinline__ void add_prod2(const HD<float, C> &a, const HD<float, C> &b, const HD<float, C> &c,
+                                              const HD<float, C> &d)
+    {
+        chd_add(s, hfma(a, b, hmul(c, d)));
+    }
+    __device__ __forceinline__ void add_prod(const HD<float, C> &a, const HD<float, C> &b)
+    {
+        chd_add(s, hmul(a, b));
+    }
+    __device__ __forceinline__ HD<float, C> value() const { return chd_value(s); }
+};
+
+template <typename T>
+struct IsComp {
+    static constexpr bool value = false;
+};
+template <>
+struct IsComp<float> {
+    static constexpr bool value = true;
+};
+
+// ------------------------------------------------------------------ functions
+// Rosenbrock, f = sum_{k<n-1} 100 (x_{k+1} - x_k^2)^2 + (1 - x_k)^2, on hDuals.
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, int n, int i, int cstart)
+{
+    TermSum<T, C, IsComp<T>::value> acc;
+    acc.init();
+    HD<T, C> y0 = seed<T, C>(xs[0], 0, i, cstart);
+    for (int k = 0; k + 1 < n; ++k) {
+        const HD<T, C> y1 = seed<T, C>(xs[k + 1], k + 1, i, cstart);
+        const HD<T, C> d = hsub(y1, hmul(y0, y0));  // x_{k+1} - x_k^2
+        const HD<T, C> w = smul(T(100), d);           // 100 (x_{k+1} - x_k^2)
+        const HD<T, C> e = rsub(T(1), y0);            // 1 - x_k
+        acc.add_prod2(w, d, e, e);                    // += 100 d^2 + e^2
+        y0 = y1;
+    }
+    return acc.value();
+}
+
+// Ackley on hDuals.  S = sum y_k^2 and Cs = sum cos(2 pi y_k) are accumulated
+// in the sweep for their derivative components; their value components are
+// the per-point FP64 sums from the table.  Each derivative component of S and
+// Cs receives at most one nonzero term under CHUNK-INIT seeding (y_k carries
+// a nonzero d/dx only for k == i or k in the chunk), so these sums are exact
+// up to that term's own rounding and need no compensation.
+template <typename T, int C>
+__device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const T *__restrict__ dcos1,
+                                                 const T *__restrict__ dcos2, const T *__restrict__ sc, int n,
+                                                 int i, int cstart)
+{
+    HD<T, C> S = hzero<T, C>();
+    HD<T, C> Cs = hzero<T, C>();
+    for (int k = 0; k < n; ++k) {
+        const HD<T, C> y = seed<T, C>(xs[k], k, i, cstart);
+        S = hfma(y, y, S);
+        // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
+        add_unary<false>(Cs, y, T(0), dcos1[k], dcos2[k]);
+    }
+    S.v = sc[0];   // sum x_k^2        (FP64 island)
+    Cs.v = sc[1];  // sum cos(2 pi x_k) (FP64 island)
+    const T inv_n = sc[2];
+    const HD<T, C> a = smul(inv_n, S);                   // S/n
+    const HD<T, C> r = unary(a, sc[3], sc[4], sc[5]);    // sqrt(S/n)
+    const HD<T, C> t1 = unary(smul(T(-0.2), r), sc[6], sc[6], sc[6]);  // exp(-0.2 r)
+    const HD<T, C> t2 = unary(smul(inv_n, Cs), sc[7], sc[7], sc[7]);   // exp(Cs/n)
+    HD<T, C> f = hsub(smul(T(-20), t1), t2);
+    f.v = f.v + T(20) + T(2.718281828459045);
+    return f;
+}
+
+// ------------------------------------------------------------------ kernel
+template <typename T, int C, int FN, bool HVP, int MB>
+__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n;
+    const Smem<T> L = smem_layout<T>(FN, HVP, n, a.maxpts, a.mt);
+    T *xs = reinterpret_cast<T *>(smem_raw + L.xs);
+    T *vs = reinterpret_cast<T *>(smem_raw + L.vs);
+
+    const long long t0 = (long long)blockIdx.x * blockDim.x;
+    const long long p0 = t0 / a.tpp;
+    long long plast = (t0 + blockDim.x - 1) / a.tpp;
+    if (plast > a.batch - 1) plast = a.batch - 1;
+    const int npts = (int)(plast - p0 + 1);
+    const int tid = threadIdx.x;
+
+    // ---- stage x (and v) of this block's points: one contiguous range.
+    {
+        const T *X = reinterpret_cast<const T *>(a.x) + p0 * n;
+        const T *V = reinterpret_cast<const T *>(a.v) + p0 * n;
+        const int cnt = npts * n;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            xs[e] = X[e];
+            if (HVP) vs[e] = V[e];
+        }
+    }
+    __syncthreads();
+
+    // ---- per-point value tables (FP64 islands)
+    if (FN == FN_ACKLEY) {
+        T *t1 = reinterpret_cast<T *>(smem_raw + L.t1);
+        T *t2 = reinterpret_cast<T *>(smem_raw + L.t2);
+        T *sc = reinterpret_cast<T *>(smem_raw + L.sc);
+        const int cnt = npts * n;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            T s, c;
+            if (sizeof(T) == 8) {
+                double sd, cd;
+                sincospi(2.0 * (double)xs[e], &sd, &cd);
+                s = (T)sd;
+                c = (T)cd;
+            } else {
+                float sf, cf;
+                sincospif(2.0f * (float)xs[e], &sf, &cf);
+                s = (T)sf;
+                c = (T)cf;
+            }
+            t1[e] = T(-2.0 * CUDART_PI) * s;
+            t2[e] = T(-4.0 * CUDART_PI * CUDART_PI) * c;
+        }
+        // One warp per point: S = sum x^2 and C = sum cos(2 pi x) in FP64.
+        const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+        for (int q = warp; q < npts; q += nw) {
+            double S = 0.0, Cv = 0.0;
+            for (int k = lane; k < n; k += 32) {
+                const double xv = (double)xs[q * n + k];
+                S = fma(xv, xv, S);
+                Cv += (double)t2[q * n + k] * (-1.0 / (4.0 * CUDART_PI * CUDART_PI));
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                S += __shfl_xor_sync(0xffffffffu, S, off);
+                Cv += __shfl_xor_sync(0xffffffffu, Cv, off);
+            }
+            if (lane == 0) {
+                const double nn = (double)n;
+                const double a0 = S / nn;
+                const double sq = sqrt(a0);
+                T *o = sc + q * kAckScal;
+                o[0] = (T)S;
+                o[1] = (T)Cv;
+                o[2] = (T)(1.0 / nn);
+                o[3] = (T)sq;                        // sqrt at S/n
+                o[4] = (T)(0.5 / sq);                // its first derivative
+                o[5] = (T)(-0.25 / (sq * a0));       // its second derivative
+                o[6] = (T)exp(-0.2 * sq);            // exp at -0.2 sqrt(S/n)
+                o[7] = (T)exp(Cv / nn);              // exp at C/n
+            }
+        }
+        __syncthreads();
+    } else if (FN == FN_FP) {
+        T *ts = reinterpret_cast<T *>(smem_raw + L.t1);
+        T *tc = reinterpret_cast<T *>(smem_raw + L.t2);
+        T *res = reinterpret_cast<T *>(smem_raw + L.res);
+        double *ds = reinterpret_cast<double *>(smem_raw + L.dsin);
+        double *dc = reinterpret_cast<double *>(smem_raw + L.dcos);
+        const int cnt = npts * n;
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            double sd, cd;
+            sincos((double)xs[e], &sd, &cd);
+            ds[e] = sd;
+            dc[e] = cd;
+            ts[e] = (T)sd;
+            tc[e] = (T)cd;
+        }
+        __syncthreads();
+        // r_m = E_m - sum_j (A_mj sin x_j + B_mj cos x_j), FP64, one (point, m)
+        // pair per thread.
+        for (int e = tid; e < cnt; e += blockDim.x) {
+            const int q = e / n, m = e - q * n;
+            const double *Ar = a.A + (size_t)m * a.ld;
+            const double *Br = a.B + (size_t)m * a.ld;
+            const double *sq = ds + q * n;
+            const double *cq = dc + q * n;
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s = fma(Ar[j], sq[j], fma(Br[j], cq[j], s));
+            res[e] = (T)(a.E[m] - s);
+        }
+        __syncthreads();
+    }
+
+    // ---- this thread's (point, row, lane)
+    const long long gid = t0 + tid;
+    const long long p = gid / a.tpp;
+    const int rem = (int)(gid - p * a.tpp);
+    const int i = rem / a.tpr;
+    const int r = rem - i * a.tpr;
+    const bool active = p < a.batch;
+    const int q = active ? (int)(p - p0) : 0;
+    const T *xq = xs + q * n;
+    const T *vq = vs + q * n;
+
+    using Dot = typename std::conditional<IsComp<T>::value, CSum, T>::type;
+    Dot dot;
+    if constexpr (IsComp<T>::value) {
+        dot.s = 0.f;
+        dot.e = 0.f;
+    } else {
+        dot = T(0);
+    }
+
+    auto emit = [&](const HD<T, C> &f, int cstart) {
+        if constexpr (HVP) {
+#pragma unroll
+            for (int l = 0; l < C; ++l) {
+                if (cstart + l < n) {
+                    if constexpr (IsComp<T>::value) cdot_add(dot, f.h[l], vq[cstart + l]);
+                    else dot = fma_(f.h[l], vq[cstart + l], dot);
+                }
+            }
+        } else {
+            if (active) {
+                T *H = reinterpret_cast<T *>(a.out) + ((size_t)p * n + i) * n;
+#pragma unroll
+                for (int l = 0; l < C; ++l)
+                    if (cstart + l < n) H[cstart + l] = f.h[l];
+            }
+        }
+    };
+
+    if constexpr (FN == FN_ROSENBROCK) {
+        for (int j = r; j < a.nch; j += a.tpr) {
+            const int cstart = j * C;
+            emit(rosenbrock_sweep<T, C>(xq, n, i, cstart), cstart);
+        }
+    } else if constexpr (FN == FN_ACKLEY) {
+        const T *t1 = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
+        const T *t2 = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
+        const T *sc = reinterpret_cast<const T *>(smem_raw + L.sc) + q * kAckScal;
+        for (int j = r; j < a.nch; j += a.tpr) {
+            const int cstart = j * C;
+            emit(ackley_sweep<T, C>(xq, t1, t2, sc, n, i, cstart), cstart);
+        }
+    } else {
+        // Fletcher-Powell: f = sum_m r_m^2, r_m = E_m - sum_j (A_mj sin y_j +
+        // B_mj cos y_j).  A and B stream through shared memory in tiles of mt
+        // rows, stored transposed ([j][m]) so a thread reads MB consecutive
+        // rows per j; MB residual hDuals are accumulated in registers at once
+        // so each seeded y_j is reused MB times.  All threads of the block walk
+        // the tiles together (uniform trip counts around __syncthreads).
+        const T *ts = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
+        const T *tc = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
+        const T *res = reinterpret_cast<const T *>(smem_raw + L.res) + q * n;
+        T *At = reinterpret_cast<T *>(smem_raw + L.at);
+        T *Bt = reinterpret_cast<T *>(smem_raw + L.bt);
+        const int mt = a.mt;
+        const int ntiles = (n + mt - 1) / mt;
+        const int iters = (a.nch + a.tpr - 1) / a.tpr;
+        for (int it = 0; it < iters; ++it) {
+            const int j = r + it * a.tpr;
+            const bool has = j < a.nch;
+            const int cstart = j * C;
+            TermSum<T, C, IsComp<T>::value> acc;
+            acc.init();
+            for (int tile = 0; tile < ntiles; ++tile) {
+                const int m0 = tile * mt;
+                if (ntiles > 1 || it == 0) {
+                    __syncthreads();
+                    const int cnt = mt * n;
+                    for (int e = tid; e < cnt; e += blockDim.x) {
+                        const int mm = e / n, jj = e - mm * n;
+                        const int m = m0 + mm;
+                        T av = T(0), bv = T(0);
+                        if (m < n) {
+                            av = (T)a.A[(size_t)m * a.ld + jj];
+                            bv = (T)a.B[(size_t)m * a.ld + jj];
+                        }
+                        At[jj * mt + mm] = av;
+                        Bt[jj * mt + mm] = bv;
+                    }
+                    __syncthreads();
+                }
+                if (!has) continue;
+                const int mend = min(m0 + mt, n);
+                for (int mb = m0; mb < mend; mb += MB) {
+                    HD<T, C> s[MB];
+#pragma unroll
+                    for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
+                    for (int jv = 0; jv < n; ++jv) {
+                        const HD<T, C> y = seed<T, C>(xq[jv], jv, i, cstart);
+                        const T sj = ts[jv], cj = tc[jv];
+                        const T *ar = At + jv * mt + (mb - m0);
+                        const T *br = Bt + jv * mt + (mb - m0);
+#pragma unroll
+                        for (int u = 0; u < MB; ++u) {
+                            sfma_unary<false>(s[u], ar[u], y, sj, cj, -sj);   // + A_mj sin y_j
+                            sfma_unary<false>(s[u], br[u], y, cj, -sj, -cj);  // + B_mj cos y_j
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < MB; ++u) {
+                        if (mb + u < mend) {
+                            HD<T, C> rr = rsub(T(0), s[u]);
+                            rr.v = res[mb + u];  // E_m - sum_j (...)  (FP64 island)
+                            acc.add_prod(rr, rr);
+                        }
+                    }
+                }
+            }
+            if (has) emit(acc.value(), cstart);
+        }
+    }
+
+    if constexpr (HVP) {
+        // Sum the tpr lanes of the row (aligned groups inside one warp).
+        if constexpr (IsComp<T>::value) {
+            for (int off = a.tpr >> 1; off > 0; off >>= 1) {
+                CSum o;
+                o.s = __shfl_xor_sync(0xffffffffu, dot.s, off);
+                o.e = __shfl_xor_sync(0xffffffffu, dot.e, off);
+                dot = csum_merge(dot, o);
+            }
+            if (active && r == 0) reinterpret_cast<float *>(a.out)[(size_t)p * n + i] = csum_value(dot);
+        } else {
+            for (int off = a.tpr >> 1; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
+            if (active && r == 0) reinterpret_cast<T *>(a.out)[(size_t)p * n + i] = dot;
+        }
+    }
+}
+
+// Host-side launch helper: computes the layout, opts into large dynamic
+// shared memory once per (kernel, device), launches, and reports the error.
+template <typename T, int C, int FN, bool HVP, int MB>
+cudaError_t launch_sweep(SweepArgs a, int block_threads, cudaStream_t stream)
+{
+    const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
+    auto kern = sweep_kernel<T, C, FN, HVP, MB>;
+    if (L.total > 48 * 1024) {
+        static int configured[64] = {0};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 0 || dev >= 64) dev = 0;
+        if (configured[dev] < (int)L.total) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+            if (e != cudaSuccess) return e;
+            configured[dev] = (int)L.total;
+        }
+    }
+    const long long threads = a.batch * (long long)a.tpp;
+    const long long blocks = (threads + block_threads - 1) / block_threads;
+    kern<<<(unsigned)blocks, block_threads, L.total, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace chessfad

@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/chessfad.h declares, and rejects bad
+arguments with the documented status codes before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2410_22575_gb300 as cf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"CHESSFAD_API\s+[\w\s\*]*?\b(chessfad_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cf.load()
+    names = _declared()
+    assert len(names) >= 10
+    for name in sorted(names):
+        assert hasattr(lib, name), name
+
+
+def test_version_and_strerror():
+    assert cf.chessfad_version() >= 100
+    assert cf.strerror(0) == "success"
+    for code in range(-11, 0):
+        assert cf.strerror(code) != "unknown status"
+    assert cf.strerror(-99) == "unknown status"
+
+
+def test_argument_errors_without_gpu():
+    lib = cf.load()
+    dummy = ctypes.c_void_p(16)
+    # function id, size, batch, chunk, precision, null pointers: rejected on the host
+    assert lib.chessfad_hvp(3, 8, 4, 4, dummy, dummy, dummy, None, 0, None) == -1
+    assert lib.chessfad_hvp(0, 0, 4, 4, dummy, dummy, dummy, None, 0, None) == -2
+    assert lib.chessfad_hvp(0, 513, 4, 4, dummy, dummy, dummy, None, 0, None) == -2
+    assert lib.chessfad_hvp(0, 8, -1, 4, dummy, dummy, dummy, None, 0, None) == -3
+    assert lib.chessfad_hvp(0, 8, 4, 3, dummy, dummy, dummy, None, 0, None) == -4
+    assert lib.chessfad_hvp(0, 8, 4, 64, dummy, dummy, dummy, None, 0, None) == -4
+    assert lib.chessfad_hvp(0, 8, 4, 4, None, dummy, dummy, None, 0, None) == -5
+    assert lib.chessfad_hvp(0, 8, 4, 4, dummy, None, dummy, None, 0, None) == -5
+    assert lib.chessfad_hessian(0, 8, 4, 4, dummy, None, None, 0, None) == -5
+    assert lib.chessfad_hvp(0, 8, 4, 4, dummy, dummy, dummy, None, 7, None) == -7
+    # Fletcher-Powell needs parameters with ld >= n
+    assert lib.chessfad_hvp(2, 8, 4, 4, dummy, dummy, dummy, None, 0, None) == -6
+    p = cf.FPParams(16, 16, 16, 4)
+    assert lib.chessfad_hvp(2, 8, 4, 4, dummy, dummy, dummy, ctypes.byref(p), 0, None) == -6
+    # batch == 0 is a no-op that succeeds without touching the device
+    assert lib.chessfad_hvp(0, 8, 0, 4, None, None, None, None, 0, None) == 0
+    # bad launch configurations
+    bad = cf.Config(4, 3, 256)
+    assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
+    bad = cf.Config(4, 4, 1024)
+    assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
+    bad = cf.Config(5, 4, 256)
+    assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
+
+
+@pytest.mark.parametrize("fn", [0, 1, 2])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_default_config_host_only(fn, prec):
+    for n in (1, 2, 16, 33, 64, 256, 512):
+        c = cf.chessfad_default_config(fn, n, 1000, prec)
+        assert c.csize in (1, 2, 4, 8, 16, 32)
+        assert c.csize <= max(1, 1 << (n - 1).bit_length())
+        nch = -(-n // c.csize)
+        assert 1 <= c.threads_per_row <= 32 and c.threads_per_row & (c.threads_per_row - 1) == 0
+        assert c.threads_per_row <= max(1, 1 << (nch - 1).bit_length())
+        assert c.block_threads % 32 == 0
+
+
+def test_product_path_has_no_oracle_import():
+    """The package never imports the oracle (the oracle is test infrastructure)."""
+    pkg = os.path.join(ROOT, "paper_2410_22575_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text, f

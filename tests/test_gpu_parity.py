@@ -1,0 +1,140 @@
+"""Parity of the CUDA path with the FP64 oracle, element by element, through
+the C ABI.  Bounds (per point, normalised by ||H||_F ||v||_2, or ||H||_F for a
+Hessian): 1e-12 for FP64 and 1e-5 for compensated FP32.  For FP32 the oracle
+receives the same float-rounded inputs the device holds."""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2410_22575_gb300 as cf
+from paper_2410_22575_gb300 import workloads as W
+
+from gpu_helpers import BOUND, Dev, hessian_err, hvp_err
+
+pytestmark = pytest.mark.gpu
+
+FNS = [W.ROSENBROCK, W.ACKLEY, W.FLETCHER_POWELL]
+PRECS = [cf.FP64, cf.FP32_COMP]
+CHUNKS = [1, 2, 4, 8, 16, 32]
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("c", CHUNKS)
+def test_hvp_and_hessian_every_chunk(fn, prec, c):
+    # n = 19: ragged last chunk for every c > 1, rows spanning several lanes;
+    # 150 points: several CTAs and a partial last CTA.
+    d = Dev(W.make_batch(fn, 19, 150, seed=10 + c), prec)
+    e = hvp_err(d, d.hvp(csize=c))
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+    e = hessian_err(d, d.hessian(csize=c))
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 31, 64])
+def test_sizes(fn, prec, n):
+    d = Dev(W.make_batch(fn, n, 97, seed=100 + n), prec)
+    for c in (1, 4, 16):
+        e = hvp_err(d, d.hvp(csize=c))
+        assert e.max() <= BOUND[prec], (c, e.max())
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+def test_launch_configurations(fn, prec):
+    d = Dev(W.make_batch(fn, 24, 70, seed=7), prec)
+    ref = None
+    for c in (2, 8):
+        nch = -(-24 // c)
+        for tpr in (1, 2, 4, 8, 16, 32):
+            for bt in (32, 96, 256):
+                cfg = cf.Config(c, tpr, bt)
+                out = d.hvp(cfg=cfg)
+                e = hvp_err(d, out)
+                assert e.max() <= BOUND[prec], (c, tpr, bt, e.max())
+        H = d.hessian(cfg=cf.Config(c, 4, 64))
+        assert hessian_err(d, H).max() <= BOUND[prec]
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+def test_max_size(fn, prec):
+    # n = CHESSFAD_MAX_N at a few points; FP at this size streams A/B tiles.
+    d = Dev(W.make_batch(fn, 512, 2 if fn == W.FLETCHER_POWELL else 3, seed=5), prec)
+    c = 32 if prec == cf.FP32_COMP else 16
+    e = hvp_err(d, d.hvp(csize=c))
+    assert e.max() <= BOUND[prec], e.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fletcher_powell_tiled_rows(prec):
+    # n = 300 does not fit one shared-memory tile of A and B; also ld > n.
+    rng = np.random.Generator(np.random.PCG64(3))
+    inst = W.draw_fp_instance(rng, 320).leading(300)
+    A = np.zeros((300, 320)); A[:, :300] = inst.A
+    B = np.zeros((300, 320)); B[:, :300] = inst.B
+    b = W.Batch("fp300", W.FLETCHER_POWELL, 300, rng.uniform(-math.pi, math.pi, (3, 300)),
+                rng.uniform(-1, 1, (3, 300)), W.FPInstance(inst.alpha, A, B, inst.E))
+    d = Dev(b, prec)
+    for c in (4, 8):
+        e = hvp_err(d, d.hvp(csize=c))
+        assert e.max() <= BOUND[prec], (c, e.max())
+
+
+def test_batch_zero_and_nan_propagation():
+    import torch
+
+    b = W.make_batch(W.ACKLEY, 9, 20, seed=1)
+    b.x[3, 2] = np.nan
+    d = Dev(b, cf.FP64)
+    out = d.hvp(csize=4)
+    assert np.all(np.isnan(out[3]))
+    ok = np.ones(20, bool)
+    ok[3] = False
+    assert np.all(np.isfinite(out[ok]))
+    z = torch.zeros((0, 9), dtype=torch.float64, device="cuda:0")
+    assert cf.chessfad_hvp(W.ACKLEY, 9, 0, 4, z, z, z, None, cf.FP64) == 0
+
+
+def test_fp64_bitwise_deterministic_and_point_independent():
+    d = Dev(W.make_batch(W.FLETCHER_POWELL, 17, 64, seed=2), cf.FP64)
+    a = d.hvp(csize=4)
+    b = d.hvp(csize=4)
+    assert np.array_equal(a, b)
+    # permuting the batch permutes the outputs bit for bit (points are independent)
+    perm = np.random.Generator(np.random.PCG64(0)).permutation(64)
+    bp = W.Batch("p", d.b.fn, d.b.n, d.b.x[perm], d.b.v[perm], d.b.fp)
+    dp = Dev(bp, cf.FP64)
+    assert np.array_equal(dp.hvp(csize=4), a[perm])
+
+
+def test_side_stream():
+    import torch
+
+    d = Dev(W.make_batch(W.ROSENBROCK, 16, 50, seed=4), cf.FP32_COMP)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        out = cf.hvp(W.ROSENBROCK, d.x, d.v, csize=4, prec=cf.FP32_COMP, stream=s)
+    s.synchronize()
+    e = hvp_err(d, out.double().cpu().numpy())
+    assert e.max() <= BOUND[cf.FP32_COMP]
+
+
+def test_hessian_symmetry_within_bound():
+    for prec in PRECS:
+        d = Dev(W.make_batch(W.ACKLEY, 20, 10, seed=8), prec)
+        H = d.hessian(csize=8)
+        asym = np.linalg.norm(H - np.swapaxes(H, 1, 2), axis=(1, 2)) / np.linalg.norm(H, axis=(1, 2))
+        assert asym.max() <= 2 * BOUND[prec]
+
+
+def test_kernel_info_and_peak():
+    info = cf.chessfad_kernel_info(W.ACKLEY, cf.FP32_COMP, 8, True)
+    assert 16 <= info["registers"] <= 255 and info["local_bytes"] >= 0
+    f32 = cf.chessfad_peak_flops(cf.FP32_COMP)
+    f64 = cf.chessfad_peak_flops(cf.FP64)
+    assert 1e13 < f32 < 2e14
+    assert 1e11 < f64 < f32

@@ -1,0 +1,48 @@
+"""Parity at the full sizes of the named workloads, in the launch
+configurations the benchmark times, compared with the oracle point by point
+(the oracle's closed forms finish every point in seconds)."""
+import numpy as np
+import pytest
+
+import paper_2410_22575_gb300 as cf
+from paper_2410_22575_gb300 import workloads as W
+
+from gpu_helpers import BOUND, Dev, hessian_err, hvp_err
+
+pytestmark = pytest.mark.gpu
+
+
+def test_rosenbrock_n16_fp64_c4_hvp_and_hessian():
+    d = Dev(W.workload("rosenbrock_n16"), cf.FP64)
+    e = hvp_err(d, d.hvp(csize=4))
+    assert e.max() <= BOUND[cf.FP64]
+    e = hessian_err(d, d.hessian(csize=4))
+    assert e.max() <= BOUND[cf.FP64]
+
+
+@pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
+@pytest.mark.parametrize("c", [4, 8, 16, 32])
+def test_ackley_n64_chunk_sweep(prec, c):
+    if prec == cf.FP64 and c == 32:
+        pytest.skip("FP64 c=32 spills registers; covered at small sizes")
+    d = Dev(W.workload("ackley_n64"), prec)
+    e = hvp_err(d, d.hvp(csize=c))
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+
+
+@pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
+def test_fletcher_powell_n32(prec):
+    d = Dev(W.workload("fletcher_powell_n32"), prec)
+    e = hvp_err(d, d.hvp())
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+
+
+@pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
+def test_rosenbrock_n256_hessian_and_hvp(prec):
+    d = Dev(W.workload("rosenbrock_n256"), prec)
+    e = hvp_err(d, d.hvp())
+    assert e.max() <= BOUND[prec]
+    H = d.hessian()
+    for lo in range(0, 1024, 128):  # bounded host memory for the reference
+        rows = slice(lo, lo + 128)
+        assert hessian_err(d, H, rows).max() <= BOUND[prec]
