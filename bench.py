@@ -1,0 +1,421 @@
+#!/usr/bin/env python3
+"""Benchmark: Hessian-vector products per second on one GB300 (and N GPUs).
+
+Workload: Ackley, n = 64, 65536 points, x ~ U[-5,5], v ~ U[-1,1], seed 1
+(PCG64), the configuration the headline metric is quoted on.  One step is one
+``chessfad_hvp`` call over the whole batch: seeding, chunked-hDual propagation,
+row-times-v products and the in-kernel row reduction, all in the library's
+sweep kernel.  The headline ``value`` is compensated-FP32 HVP/s with inputs
+resident in HBM; the FP64 rate, a chunk-size sweep and the end-to-end rate
+through host buffers are reported beside it.
+
+Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
+on the launching stream, with a 256 MiB buffer written between steps to flush
+the 129 MB L2 (outside the events).  Barrier + synchronize on both sides, max
+over ranks.  Under torchrun every rank runs the same per-GPU batch (weak
+scaling; points are independent, there is no collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle (the paper's sequential
+CHESS-VEC, Alg. 7, OpenMP over points) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Hessian-vector products/sec per function and n, FP32-comp vs FP64, 1 GB300"
+WORKLOAD = "ackley_n64"
+WORKLOAD_DESC = "Ackley n=64, 65536 points, x~U[-5,5], v~U[-1,1], seed 1 (PCG64)"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+# FP64 DFMA lanes per SM: GB300's nominal 1.25 TFLOP/s FP64 at 2070 MHz over
+# 152 SMs is 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM.
+FP64_LANES_PER_SM = 2
+
+
+def model_flops_ackley(n: int, c: int) -> float:
+    """Model flops of one Ackley HVP by the dense chunked-hDual method (the
+    Sec. V operation model extended to Ackley's op list; FMA = 2):
+    n*nch*[n(20c+12) + 22c+18] + 2n^2."""
+    nch = -(-n // c)
+    return n * nch * (n * (20 * c + 12) + 22 * c + 18) + 2 * n * n
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        load = [s for s in sm if s > 0.5 * (max(mx) if mx else 0)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("CHESSFAD_BENCH_GLOO") is None else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(world, value: float, device) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ GPU arm
+def timed_steps(fn_step, steps, warmup, stream, flush_buf):
+    """Per-step CUDA-event durations (ms) of fn_step, L2 flushed in between."""
+    import torch
+
+    for _ in range(warmup):
+        fn_step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush_buf.add_(1)  # 256 MiB write, outside the events
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn_step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cf.load()
+    b = W.workload(WORKLOAD)
+    fn, n, batch = b.fn, b.n, b.batch
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    res = {}
+    for prec, dt in ((cf.FP32_COMP, torch.float32), (cf.FP64, torch.float64)):
+        x = torch.tensor(b.x, dtype=dt, device=dev)
+        v = torch.tensor(b.v, dtype=dt, device=dev)
+        out = torch.empty_like(x)
+        cfg = cf.chessfad_autotune_hvp(fn, n, batch, x, v, out, None, prec, stream)
+        steps = args.steps if prec == cf.FP32_COMP else max(1, min(args.steps, args.fp64_steps))
+
+        def step():
+            st = cf.chessfad_hvp(fn, n, batch, 0, x, v, out, None, prec, stream)
+            if st != 0:
+                raise cf.ChessfadError(st, "chessfad_hvp")
+
+        barrier(world)
+        torch.cuda.synchronize()
+        if prec == cf.FP32_COMP:
+            with ClockSampler(local) as clk:
+                ms = timed_steps(step, steps, args.warmup, stream, flush)
+            clocks = clk.summary()
+        else:
+            ms = timed_steps(step, steps, args.warmup, stream, flush)
+        torch.cuda.synchronize()
+        barrier(world)
+        tot = max_over_ranks(world, sum(ms), dev)
+        res[prec] = {"cfg": cfg.as_dict(), "ms": ms, "total_ms": tot, "steps": steps,
+                     "out_sample": out[:256].double().cpu().numpy(), "x32": x[:256].double().cpu().numpy(),
+                     "v32": v[:256].double().cpu().numpy()}
+        if prec == cf.FP32_COMP:
+            res[prec]["clocks"] = clocks
+
+        # chunk-size sweep (shorter), same precision
+        sweep = {}
+        for c in (4, 8, 16, 32):
+            info = cf.chessfad_kernel_info(fn, prec, c, True)
+            if info["local_bytes"] > 0:
+                sweep[str(c)] = {"skipped": "spills registers", **info}
+                continue
+
+            def stc(c=c):
+                st = cf.chessfad_hvp(fn, n, batch, c, x, v, out, None, prec, stream)
+                if st != 0:
+                    raise cf.ChessfadError(st, "chessfad_hvp")
+
+            k = max(1, min(5, steps))
+            m = timed_steps(stc, k, 1, stream, flush)
+            t = max_over_ranks(world, sum(m), dev) / k
+            sweep[str(c)] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t, **info}
+        res[prec]["sweep"] = sweep
+        del x, v, out
+
+    # ---- end to end: pinned host buffers -> device -> hvp -> host, FP32-comp
+    xh = torch.tensor(b.x, dtype=torch.float32).pin_memory()
+    vh = torch.tensor(b.v, dtype=torch.float32).pin_memory()
+    oh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(xh, device=dev)
+    vd = torch.empty_like(vh, device=dev)
+    od = torch.empty_like(xh, device=dev)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        st = cf.chessfad_hvp(fn, n, batch, 0, xd, vd, od, None, cf.FP32_COMP, stream)
+        if st != 0:
+            raise cf.ChessfadError(st, "chessfad_hvp")
+        oh.copy_(od, non_blocking=True)
+
+    barrier(world)
+    ms_e2e = timed_steps(e2e_step, args.steps, args.warmup, stream, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    tot_e2e = max_over_ranks(world, sum(ms_e2e), dev)
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
+
+    f32 = res[cf.FP32_COMP]
+    f64 = res[cf.FP64]
+    value = world * batch * f32["steps"] / (f32["total_ms"] * 1e-3)
+    v64 = world * batch * f64["steps"] / (f64["total_ms"] * 1e-3)
+    c = f32["cfg"]["csize"]
+    flops_launch = model_flops_ackley(n, c) * batch
+    avg_ms = sum(f32["ms"]) / len(f32["ms"])
+    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    peak_fp64 = SM_COUNT * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
+    achieved = flops_launch / (avg_ms * 1e-3)
+    try:
+        micro32 = cf.chessfad_peak_flops(cf.FP32_COMP)
+        micro64 = cf.chessfad_peak_flops(cf.FP64)
+    except Exception as e:  # report, do not hide
+        micro32 = micro64 = None
+        print(f"peak microbenchmark failed: {e}", file=sys.stderr)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        tj = json.load(open(tfile))
+        ent = tj.get(f"{WORKLOAD}/fp32_comp/c{c}")
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent.get("dram_bytes_per_launch")
+    c64 = f64["cfg"]["csize"]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "HVP/s",
+        "n_gpus": world,
+        "steps": f32["steps"],
+        "warmup": args.warmup,
+        "ms_per_step": f32["total_ms"] / f32["steps"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 (compensated; f64 islands)",
+        "data": "synthetic (seeded PCG64 draws of the workload's distributions)",
+        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": n, "batch": batch,
+                   "precision": "fp32_comp", **f32["cfg"], "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world} (points independent, no collective)"},
+        "fp64": {"value": v64, "unit": "HVP/s", "steps": f64["steps"], "ms_per_step": f64["total_ms"] / f64["steps"],
+                 **{k: v for k, v in f64["cfg"].items()},
+                 "model_tflops": model_flops_ackley(n, c64) * batch / (f64["total_ms"] / f64["steps"] * 1e-3) / 1e12,
+                 "peak_tflops_derived": peak_fp64 / 1e12},
+        "fp32_over_fp64": value / v64,
+        "chunk_sweep": {"fp32_comp": f32["sweep"], "fp64": f64["sweep"]},
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
+                     "frac": achieved / peak_fp32, "traffic": traffic,
+                     "flops_per_launch": flops_launch, "kernel": "sweep_kernel<float,%d,ACKLEY,HVP>" % c,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "peak_microbench": None if micro32 is None else micro32 / 1e12,
+                     "frac_of_microbench": None if micro32 is None else achieved / micro32,
+                     "fp64_peak_microbench": None if micro64 is None else micro64 / 1e12},
+        "e2e": {"value": world * batch * args.steps / (tot_e2e * 1e-3), "unit": "HVP/s",
+                "h2d_bytes_per_step": 2 * batch * n * 4, "d2h_bytes_per_step": batch * n * 4},
+        "gpu_launches": f32["steps"],
+        "clocks": f32.get("clocks"),
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(b, c, f32, f64, args)
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_sample_time(b, c, target_s):
+    """Time the oracle's CHESS-VEC (Alg. 7, FP64, OpenMP over points) on a
+    prefix of the batch sized for about target_s seconds; return
+    (hvp_per_s, sample_points, seconds, outputs)."""
+    import oracle
+
+    oracle.build()
+    probe = 64
+    t0 = time.perf_counter()
+    oracle.chess_vec(b.fn, b.x[:probe], b.v[:probe], c)
+    dt = time.perf_counter() - t0
+    m = int(min(b.batch, max(probe, probe * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    out = oracle.chess_vec(b.fn, b.x[:m], b.v[:m], c)
+    dt = time.perf_counter() - t0
+    return m / dt, m, dt, out
+
+
+def cpu_baseline(b, c, f32, f64, args):
+    import numpy as np
+
+    import oracle
+    from paper_2410_22575_gb300 import metrics
+
+    rate, m, dt, _ = cpu_sample_time(b, c, args.cpu_seconds)
+    # closed-form oracle (O1) on the same prefix, and the GPU's error against it
+    t0 = time.perf_counter()
+    oracle.hvp(b.fn, b.x[:m], b.v[:m])
+    t_cf = time.perf_counter() - t0
+    acc = {}
+    for name, r in (("fp32_comp", f32), ("fp64", f64)):
+        ref, hn = oracle.hvp(b.fn, r["x32"], r["v32"], with_norm=True)
+        e = metrics.hvp_errors(r["out_sample"], ref, hn, r["v32"])
+        acc[name] = metrics.summary(e)
+    return {"value": rate, "unit": "HVP/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {m} of {b.batch} points, CHESS-VEC (Alg. 7) FP64 with c={c}, {dt:.1f} s",
+            "closed_form_hvp_per_s": m / t_cf,
+            "gpu_error_vs_oracle_first256": acc}
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2410_22575_gb300 import workloads as W
+
+    b = W.workload(WORKLOAD)
+    c = 16
+    per = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_sample_time(b, c, per / 4)
+    rates, secs, ms = [], 0.0, []
+    sample = 0
+    for _ in range(args.steps):
+        r, m, dt, _ = cpu_sample_time(b, c, per)
+        rates.append(r)
+        secs += dt
+        sample = m
+        ms.append(dt * 1e3 * b.batch / m)
+    value = statistics.median(rates)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "HVP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded PCG64 draws of the workload's distributions)",
+        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": 64, "batch": b.batch,
+                   "precision": "fp64", "csize": c},
+        "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"each step: first {sample} of {b.batch} points, CHESS-VEC (Alg. 7) FP64, c={c}"},
+        "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--impl", choices=["chessfad", "reference"], default="chessfad")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

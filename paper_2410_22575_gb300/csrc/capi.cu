@@ -117,6 +117,16 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
     if (fn == CHESSFAD_FLETCHER_POWELL && a.mt % fp_mb(c.csize) != 0) return CHESSFAD_ERR_CONFIG;
     cudaError_t e = cudaErrorInvalidValue;
     const bool f64 = (prec == CHESSFAD_FP64);
+    if (!f64 && n == 1) {
+        // One variable: compute in FP64 (float I/O), see dispatch.h.
+        a.nch = 1;
+        switch (fn) {
+        case CHESSFAD_ROSENBROCK: e = launch_rosenbrock_f64io32(hvp, a, c.block_threads, stream); break;
+        case CHESSFAD_ACKLEY: e = launch_ackley_f64io32(hvp, a, c.block_threads, stream); break;
+        case CHESSFAD_FLETCHER_POWELL: e = launch_fp_f64io32(hvp, a, c.block_threads, stream); break;
+        }
+        return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+    }
     switch (fn) {
     case CHESSFAD_ROSENBROCK:
         e = f64 ? launch_rosenbrock_f64(c.csize, hvp, a, c.block_threads, stream)

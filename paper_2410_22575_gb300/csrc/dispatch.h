@@ -22,6 +22,13 @@ CHESSFAD_DECL(launch_fp_f64);
 CHESSFAD_DECL(launch_fp_f32c);
 #undef CHESSFAD_DECL
 
+// n == 1 under CHESSFAD_FP32_COMP: the Hessian is one entry, a sum of terms
+// that can cancel to far below their size; the single sweep runs in FP64 with
+// float inputs and output.
+cudaError_t launch_rosenbrock_f64io32(bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream);
+cudaError_t launch_ackley_f64io32(bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream);
+cudaError_t launch_fp_f64io32(bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream);
+
 // cudaFuncGetAttributes of the instantiation (registers, local memory).
 #define CHESSFAD_ATTR(name) cudaError_t name(int C, bool hvp, cudaFuncAttributes *fa)
 CHESSFAD_ATTR(attr_rosenbrock_f64);

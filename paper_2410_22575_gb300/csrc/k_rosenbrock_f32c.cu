@@ -7,7 +7,7 @@ template <int C>
 static cudaError_t go(bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
 {
     constexpr int MB = fp_mb(C);
-    return hvp ? launch_sweep<float, C, FN_ROSENBROCK, true, MB>(a, bt, s) : launch_sweep<float, C, FN_ROSENBROCK, false, MB>(a, bt, s);
+    return hvp ? launch_sweep<float, float, C, FN_ROSENBROCK, true, MB>(a, bt, s) : launch_sweep<float, float, C, FN_ROSENBROCK, false, MB>(a, bt, s);
 }
 
 cudaError_t launch_rosenbrock_f32c(int C, bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
@@ -27,8 +27,8 @@ template <int C>
 static cudaError_t at(bool hvp, cudaFuncAttributes *fa)
 {
     constexpr int MB = fp_mb(C);
-    return hvp ? cudaFuncGetAttributes(fa, sweep_kernel<float, C, FN_ROSENBROCK, true, MB>)
-               : cudaFuncGetAttributes(fa, sweep_kernel<float, C, FN_ROSENBROCK, false, MB>);
+    return hvp ? cudaFuncGetAttributes(fa, sweep_kernel<float, float, C, FN_ROSENBROCK, true, MB>)
+               : cudaFuncGetAttributes(fa, sweep_kernel<float, float, C, FN_ROSENBROCK, false, MB>);
 }
 
 cudaError_t attr_rosenbrock_f32c(int C, bool hvp, cudaFuncAttributes *fa)

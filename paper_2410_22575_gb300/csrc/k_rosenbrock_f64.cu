@@ -7,7 +7,7 @@ template <int C>
 static cudaError_t go(bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
 {
     constexpr int MB = fp_mb(C);
-    return hvp ? launch_sweep<double, C, FN_ROSENBROCK, true, MB>(a, bt, s) : launch_sweep<double, C, FN_ROSENBROCK, false, MB>(a, bt, s);
+    return hvp ? launch_sweep<double, double, C, FN_ROSENBROCK, true, MB>(a, bt, s) : launch_sweep<double, double, C, FN_ROSENBROCK, false, MB>(a, bt, s);
 }
 
 cudaError_t launch_rosenbrock_f64(int C, bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
@@ -27,8 +27,8 @@ template <int C>
 static cudaError_t at(bool hvp, cudaFuncAttributes *fa)
 {
     constexpr int MB = fp_mb(C);
-    return hvp ? cudaFuncGetAttributes(fa, sweep_kernel<double, C, FN_ROSENBROCK, true, MB>)
-               : cudaFuncGetAttributes(fa, sweep_kernel<double, C, FN_ROSENBROCK, false, MB>);
+    return hvp ? cudaFuncGetAttributes(fa, sweep_kernel<double, double, C, FN_ROSENBROCK, true, MB>)
+               : cudaFuncGetAttributes(fa, sweep_kernel<double, double, C, FN_ROSENBROCK, false, MB>);
 }
 
 cudaError_t attr_rosenbrock_f64(int C, bool hvp, cudaFuncAttributes *fa)
@@ -42,6 +42,13 @@ cudaError_t attr_rosenbrock_f64(int C, bool hvp, cudaFuncAttributes *fa)
     case 32: return at<32>(hvp, fa);
     }
     return cudaErrorInvalidValue;
+}
+
+// One-variable compensated-FP32 calls: FP64 sweep, float x, v and output.
+cudaError_t launch_rosenbrock_f64io32(bool hvp, const SweepArgs &a, int bt, cudaStream_t s)
+{
+    return hvp ? launch_sweep<double, float, 1, FN_ROSENBROCK, true, fp_mb(1)>(a, bt, s)
+               : launch_sweep<double, float, 1, FN_ROSENBROCK, false, fp_mb(1)>(a, bt, s);
 }
 
 }  // namespace chessfad

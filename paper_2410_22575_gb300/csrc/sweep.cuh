@@ -189,7 +189,10 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename T, int C, int FN, bool HVP, int MB>
+// T is the arithmetic type of the sweep, IO the element type of x, v and the
+// output (IO = T except for the one-variable compensated-FP32 case, which
+// computes in FP64 with float I/O).
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,12 +210,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
 
     // ---- stage x (and v) of this block's points: one contiguous range.
     {
-        const T *X = reinterpret_cast<const T *>(a.x) + p0 * n;
-        const T *V = reinterpret_cast<const T *>(a.v) + p0 * n;
+        const IO *X = reinterpret_cast<const IO *>(a.x) + p0 * n;
+        const IO *V = reinterpret_cast<const IO *>(a.v) + p0 * n;
         const int cnt = npts * n;
         for (int e = tid; e < cnt; e += blockDim.x) {
-            xs[e] = X[e];
-            if (HVP) vs[e] = V[e];
+            xs[e] = (T)X[e];
+            if (HVP) vs[e] = (T)V[e];
         }
     }
     __syncthreads();
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             t1[e] = T(-2.0 * CUDART_PI) * s;
             t2[e] = T(-4.0 * CUDART_PI * CUDART_PI) * c;
         }
+        __syncthreads();
         // One warp per point: S = sum x^2 and C = sum cos(2 pi x) in FP64.
         const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
         for (int q = warp; q < npts; q += nw) {
@@ -331,10 +335,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             }
         } else {
             if (active) {
-                T *H = reinterpret_cast<T *>(a.out) + ((size_t)p * n + i) * n;
+                IO *H = reinterpret_cast<IO *>(a.out) + ((size_t)p * n + i) * n;
 #pragma unroll
                 for (int l = 0; l < C; ++l)
-                    if (cstart + l < n) H[cstart + l] = f.h[l];
+                    if (cstart + l < n) H[cstart + l] = (IO)f.h[l];
             }
         }
     };
@@ -434,18 +438,18 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
             if (active && r == 0) reinterpret_cast<float *>(a.out)[(size_t)p * n + i] = csum_value(dot);
         } else {
             for (int off = a.tpr >> 1; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-            if (active && r == 0) reinterpret_cast<T *>(a.out)[(size_t)p * n + i] = dot;
+            if (active && r == 0) reinterpret_cast<IO *>(a.out)[(size_t)p * n + i] = (IO)dot;
         }
     }
 }
 
 // Host-side launch helper: computes the layout, opts into large dynamic
 // shared memory once per (kernel, device), launches, and reports the error.
-template <typename T, int C, int FN, bool HVP, int MB>
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 cudaError_t launch_sweep(SweepArgs a, int block_threads, cudaStream_t stream)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
-    auto kern = sweep_kernel<T, C, FN, HVP, MB>;
+    auto kern = sweep_kernel<T, IO, C, FN, HVP, MB>;
     if (L.total > 48 * 1024) {
         static int configured[64] = {0};
         int dev = 0;
