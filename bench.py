@@ -399,6 +399,42 @@ def reference_arm(args):
     }))
 
 
+def kernel_only(args):
+    """Run only the sweep kernel of the workload in a fixed configuration
+    (W + K launches, no autotune): the command profiled with ncu."""
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    b = W.workload(args.workload, batch=args.batch)
+    prec = cf.FP64 if args.prec == "fp64" else cf.FP32_COMP
+    dt = torch.float64 if prec == cf.FP64 else torch.float32
+    x = torch.tensor(b.x, dtype=dt, device="cuda")
+    v = torch.tensor(b.v, dtype=dt, device="cuda")
+    out = torch.empty_like(x)
+    keep, params = [], None
+    if b.fn == W.FLETCHER_POWELL:
+        keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
+        params = cf.fp_params(*keep)
+    cfg = cf.Config(args.csize, args.tpr, args.block)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for k in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = cf.chessfad_hvp_config(b.fn, b.n, b.batch, cfg, x, v, out, params, prec, stream)
+        e1.record(stream)
+        if st != 0:
+            raise cf.ChessfadError(st, "chessfad_hvp_config")
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"mode": "kernel-only", "workload": args.workload, "batch": b.batch, "prec": args.prec,
+                      **cfg.as_dict(), "ms": ms, "hvp_per_s": b.batch / (min(ms) * 1e-3)}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,10 +444,19 @@ def main():
     ap.add_argument("--impl", choices=["chessfad", "reference"], default="chessfad")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--prec", choices=["fp32_comp", "fp64"], default="fp32_comp")
+    ap.add_argument("--csize", type=int, default=32)
+    ap.add_argument("--tpr", type=int, default=1)
+    ap.add_argument("--block", type=int, default=128)
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and not args.kernel_only:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.kernel_only:
+        kernel_only(args)
+    elif args.impl == "reference":
         reference_arm(args)
     else:
         gpu_arm(args)

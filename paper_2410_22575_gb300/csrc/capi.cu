@@ -22,6 +22,11 @@ static int next_pow2(int v)
     return p;
 }
 
+// Local memory per thread that is not a register spill: the FP64 sin/cos
+// argument reduction keeps a 40-byte buffer on the stack for huge arguments.
+// Frames above this size are treated as spilling kernels by the autotuner.
+static constexpr size_t kMaxFrameNoSpill = 48;
+
 static bool valid_chunk(int c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
 // Tuned configurations keyed by (fn, n, prec).
@@ -243,7 +248,7 @@ int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const v
     int rc = CHESSFAD_SUCCESS;
     for (int c : chunks) {
         cudaFuncAttributes fa{};
-        if (kernel_attr(fn, prec, c, true, &fa) != cudaSuccess || fa.localSizeBytes > 0) continue;  // spills
+        if (kernel_attr(fn, prec, c, true, &fa) != cudaSuccess || fa.localSizeBytes > kMaxFrameNoSpill) continue;
         const int nch = (n + c - 1) / c;
         const int tmax = std::min(32, next_pow2(nch));
         for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1) {

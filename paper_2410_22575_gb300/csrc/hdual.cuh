@@ -69,6 +69,25 @@ __device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart)
     return y;
 }
 
+// CHUNK-INIT seeds with the chunk position known at compile time: variable
+// k with chunk offset P = k - cstart (P outside [0, C) for variables outside
+// the chunk).  With P a constant the g part is a constant unit or zero
+// vector and costs no instructions; the arithmetic that consumes it is
+// unchanged (x * 0 cannot be folded away under IEEE rules).
+template <typename T, int C, int P>
+__device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row)
+{
+    HD<T, C> y;
+    y.v = xk;
+    y.d1 = is_row ? T(1) : T(0);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        y.g[l] = (l == P) ? T(1) : T(0);
+        y.h[l] = T(0);
+    }
+    return y;
+}
+
 // u * w (Fig. 1).
 template <typename T, int C>
 __device__ __forceinline__ HD<T, C> hmul(const HD<T, C> &a, const HD<T, C> &b)

@@ -138,6 +138,70 @@ struct IsComp<float> {
     static constexpr bool value = true;
 };
 
+// ------------------------------------------------------------------ seeding
+// The seeded variables y_0 .. y_{n-1} of one sweep (CHUNK-INIT, Alg. 4) are
+// visited in ascending order in three segments: before the chunk, the chunk,
+// after the chunk.  Outside the chunk the g part is the constant zero vector;
+// inside, when the chunk is unrolled, the constant unit vector e_{k-cstart}.
+// Only the d/dx_i seed [k == i] is data dependent.  Chunks wider than the
+// unroll limit walk their variables with the generic (select-based) seed.
+template <int C, int LIMIT>
+struct Unroll {
+    static constexpr bool value = C <= LIMIT;
+};
+
+template <int P, int END>
+struct StaticFor {
+    template <typename F>
+    __device__ __forceinline__ static void run(F &&f)
+    {
+        if constexpr (P < END) {
+            f(std::integral_constant<int, P>{});
+            StaticFor<P + 1, END>::run(f);
+        }
+    }
+};
+
+// f(k, y_k) for k = 0 .. n-1.
+template <typename T, int C, int LIMIT, typename F>
+__device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
+{
+    const int lo = min(cstart, n), hi = min(cstart + C, n);
+    for (int k = 0; k < lo; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
+    if constexpr (Unroll<C, LIMIT>::value) {
+        StaticFor<0, C>::run([&](auto P) {
+            const int k = cstart + P.value;
+            if (k < n) f(k, seed_at<T, C, P.value>(xs[k], k == i));
+        });
+    } else {
+        for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart));
+    }
+    for (int k = hi; k < n; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
+}
+
+// f(y_k, y_{k+1}) for k = 0 .. n-2 (functions whose terms couple neighbours).
+template <typename T, int C, int LIMIT, typename F>
+__device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
+{
+    const int a_end = min(cstart - 1, n - 1);
+    for (int k = 0; k < a_end; ++k) f(seed_at<T, C, -1>(xs[k], k == i), seed_at<T, C, -1>(xs[k + 1], k + 1 == i));
+    if constexpr (Unroll<C, LIMIT>::value) {
+        // pairs touching the chunk: k - cstart = t in [-1, C-1]
+        StaticFor<0, C + 1>::run([&](auto Q) {
+            constexpr int t = decltype(Q)::value - 1;
+            const int k = cstart + t;
+            if (k >= 0 && k + 1 < n)
+                f(seed_at<T, C, t>(xs[k], k == i), seed_at<T, C, t + 1>(xs[k + 1], k + 1 == i));
+        });
+    } else {
+        const int b_end = min(cstart + C, n - 1);
+        for (int k = max(cstart - 1, 0); k < b_end; ++k)
+            f(seed<T, C>(xs[k], k, i, cstart), seed<T, C>(xs[k + 1], k + 1, i, cstart));
+    }
+    for (int k = cstart + C; k < n - 1; ++k)
+        f(seed_at<T, C, -1>(xs[k], k == i), seed_at<T, C, -1>(xs[k + 1], k + 1 == i));
+}
+
 // ------------------------------------------------------------------ functions
 // Rosenbrock, f = sum_{k<n-1} 100 (x_{k+1} - x_k^2)^2 + (1 - x_k)^2, on hDuals.
 template <typename T, int C>
@@ -145,15 +209,12 @@ __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, i
 {
     TermSum<T, C, IsComp<T>::value> acc;
     acc.init();
-    HD<T, C> y0 = seed<T, C>(xs[0], 0, i, cstart);
-    for (int k = 0; k + 1 < n; ++k) {
-        const HD<T, C> y1 = seed<T, C>(xs[k + 1], k + 1, i, cstart);
+    for_each_pair<T, C, 8>(xs, n, i, cstart, [&](const HD<T, C> &y0, const HD<T, C> &y1) {
         const HD<T, C> d = hsub(y1, hmul(y0, y0));  // x_{k+1} - x_k^2
         const HD<T, C> w = smul(T(100), d);           // 100 (x_{k+1} - x_k^2)
         const HD<T, C> e = rsub(T(1), y0);            // 1 - x_k
         acc.add_prod2(w, d, e, e);                    // += 100 d^2 + e^2
-        y0 = y1;
-    }
+    });
     return acc.value();
 }
 
@@ -170,12 +231,11 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const
 {
     HD<T, C> S = hzero<T, C>();
     HD<T, C> Cs = hzero<T, C>();
-    for (int k = 0; k < n; ++k) {
-        const HD<T, C> y = seed<T, C>(xs[k], k, i, cstart);
+    for_each_seed<T, C, 16>(xs, n, i, cstart, [&](int k, const HD<T, C> &y) {
         S = hfma(y, y, S);
         // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
         add_unary<false>(Cs, y, T(0), dcos1[k], dcos2[k]);
-    }
+    });
     S.v = sc[0];   // sum x_k^2        (FP64 island)
     Cs.v = sc[1];  // sum cos(2 pi x_k) (FP64 island)
     const T inv_n = sc[2];
@@ -193,7 +253,7 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const
 // output (IO = T except for the one-variable compensated-FP32 case, which
 // computes in FP64 with float I/O).
 template <typename T, typename IO, int C, int FN, bool HVP, int MB>
-__global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
+__global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n;
@@ -401,8 +461,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
                     HD<T, C> s[MB];
 #pragma unroll
                     for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
-                    for (int jv = 0; jv < n; ++jv) {
-                        const HD<T, C> y = seed<T, C>(xq[jv], jv, i, cstart);
+                    for_each_seed<T, C, 16>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
                         const T sj = ts[jv], cj = tc[jv];
                         const T *ar = At + jv * mt + (mb - m0);
                         const T *br = Bt + jv * mt + (mb - m0);
@@ -411,7 +470,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const SweepArgs a)
                             sfma_unary<false>(s[u], ar[u], y, sj, cj, -sj);   // + A_mj sin y_j
                             sfma_unary<false>(s[u], br[u], y, cj, -sj, -cj);  // + B_mj cos y_j
                         }
-                    }
+                    });
 #pragma unroll
                     for (int u = 0; u < MB; ++u) {
                         if (mb + u < mend) {
