@@ -159,6 +159,60 @@ CHESSFAD_API int chessfad_autotune_hvp(int fn, int n, long long batch, const voi
  * the device; allocates no device memory. */
 CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s);
 
+/* ---------------------------------------------------------------------------
+ * Uneven batches: requests of different functions and sizes in one launch.
+ *
+ * Request q evaluates out[off .. off+n) = H_fn(x[off .. off+n)) v[off .. off+n)
+ * on the packed arrays xpack, vpack, outpack (element offsets, any order, the
+ * caller keeps different requests' ranges disjoint).  A Fletcher-Powell
+ * request uses the leading n x n block of the shared A, B and the n-vector
+ * E = params->E + eoff.  The paper's workload is many independent instances
+ * (Sec. VI, L0); this entry serves instances of uneven cost in one persistent
+ * launch: the host plan cuts every (function, n) group into CTA-sized tiles of
+ * the (point, row, lane) decomposition and sorts them by estimated cost, and
+ * the kernel's CTAs pull tiles from a device queue counter.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int fn;         /* CHESSFAD_ROSENBROCK / _ACKLEY / _FLETCHER_POWELL */
+    int n;          /* 1 .. CHESSFAD_MAX_N */
+    long long off;  /* element offset of x, v, out in the packed arrays */
+    long long eoff; /* Fletcher-Powell: element offset of E; ignored otherwise */
+} chessfad_request;
+
+typedef struct chessfad_ragged_plan_s *chessfad_ragged_plan;
+
+/* Build a plan (host memory, owned by the caller until
+ * chessfad_ragged_plan_destroy) from a host array of nreq requests for
+ * precision prec with chunk size csize (8 or 16; 0 = 8).  Validates every
+ * request: CHESSFAD_ERR_FUNCTION / _SIZE for a bad fn or n,
+ * CHESSFAD_ERR_PLAN for a negative offset.  Launches nothing. */
+CHESSFAD_API int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, int prec, int csize,
+                                             chessfad_ragged_plan *plan);
+CHESSFAD_API int chessfad_ragged_plan_destroy(chessfad_ragged_plan plan);
+
+/* Device workspace bytes the plan needs (tile table, request list, offsets and
+ * the queue counter), the number of tiles and the dynamic shared memory per
+ * CTA.  Any pointer may be NULL. */
+CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes, long long *ntiles,
+                                           size_t *smem_bytes);
+
+/* Copy the plan's tables into a caller-allocated device workspace of at least
+ * workspace_bytes (cudaMemcpyAsync on stream from the plan's host memory;
+ * synchronise the stream before destroying the plan).  Once per workspace. */
+CHESSFAD_API int chessfad_ragged_plan_upload(chessfad_ragged_plan plan, void *workspace, size_t workspace_bytes,
+                                             chessfad_stream_t stream);
+
+/* Run the plan: reset the queue counter in the workspace (cudaMemsetAsync) and
+ * launch one persistent kernel, both on stream; no host synchronisation, no
+ * allocation, so the call can be captured into a CUDA graph and replayed.
+ * xpack, vpack, outpack: device, float (FP32_COMP) or double (FP64) by the
+ * plan's precision.  params: required when the plan holds Fletcher-Powell
+ * requests (ld >= their largest n).  Runs that share a workspace must not
+ * overlap on the GPU. */
+CHESSFAD_API int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpack, const void *vpack, void *outpack,
+                                     const chessfad_fp_params *params, void *workspace, size_t workspace_bytes,
+                                     chessfad_stream_t stream);
+
 /* Registers per thread and local-memory (spill) bytes per thread of the
  * HVP (hvp != 0) or Hessian kernel for (fn, prec, csize), as compiled for
  * the current device.  Host only; launches nothing. */

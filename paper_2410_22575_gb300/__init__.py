@@ -74,12 +74,20 @@ def load(build_if_missing: bool = True):
         lib.chessfad_autotune_hvp.argtypes = [I, I, L, P, P, P, P, I, P, P]
         lib.chessfad_peak_flops.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
         lib.chessfad_kernel_info.argtypes = [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(L)]
+        lib.chessfad_ragged_plan_create.argtypes = [P, L, I, I, ctypes.POINTER(P)]
+        lib.chessfad_ragged_plan_destroy.argtypes = [P]
+        lib.chessfad_ragged_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(L),
+                                                  ctypes.POINTER(ctypes.c_size_t)]
+        lib.chessfad_ragged_plan_upload.argtypes = [P, P, ctypes.c_size_t, P]
+        lib.chessfad_hvp_ragged.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
         lib.chessfad_strerror.argtypes = [I]
         lib.chessfad_strerror.restype = ctypes.c_char_p
         lib.chessfad_version.argtypes = []
         for name in ("chessfad_hvp", "chessfad_hessian", "chessfad_hvp_config", "chessfad_hessian_config",
                      "chessfad_default_config", "chessfad_autotune_hvp", "chessfad_peak_flops",
-                     "chessfad_kernel_info", "chessfad_version"):
+                     "chessfad_kernel_info", "chessfad_version", "chessfad_ragged_plan_create",
+                     "chessfad_ragged_plan_destroy", "chessfad_ragged_plan_info", "chessfad_ragged_plan_upload",
+                     "chessfad_hvp_ragged"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -216,3 +224,91 @@ def hessian(fn, x, csize=0, params=None, prec=None, stream=None, out=None, cfg=N
     else:
         _check(chessfad_hessian(fn, n, batch, csize, x, out, params, prec, stream), "chessfad_hessian")
     return out
+
+
+# ------------------------------------------------------------ uneven batches
+REQUEST_DTYPE = None
+
+
+def request_dtype():
+    """numpy dtype with the layout of chessfad_request (fn, n, off, eoff)."""
+    import numpy as np
+
+    return np.dtype([("fn", np.int32), ("n", np.int32), ("off", np.int64), ("eoff", np.int64)])
+
+
+def requests(fns, ns, offs, eoffs=None):
+    import numpy as np
+
+    r = np.zeros(len(fns), dtype=request_dtype())
+    r["fn"] = fns
+    r["n"] = ns
+    r["off"] = offs
+    r["eoff"] = 0 if eoffs is None else eoffs
+    return r
+
+
+def chessfad_ragged_plan_create(reqs, prec=FP32_COMP, csize=0):
+    """Plan handle (int) for a numpy array of requests (see request_dtype)."""
+    import numpy as np
+
+    reqs = np.ascontiguousarray(reqs, dtype=request_dtype())
+    h = ctypes.c_void_p()
+    _check(load().chessfad_ragged_plan_create(reqs.ctypes.data if len(reqs) else None, len(reqs), prec, csize,
+                                              ctypes.byref(h)), "chessfad_ragged_plan_create")
+    return h.value
+
+
+def chessfad_ragged_plan_destroy(plan) -> int:
+    return load().chessfad_ragged_plan_destroy(plan)
+
+
+def chessfad_ragged_plan_info(plan) -> dict:
+    ws = ctypes.c_size_t()
+    nt = ctypes.c_longlong()
+    sm = ctypes.c_size_t()
+    _check(load().chessfad_ragged_plan_info(plan, ctypes.byref(ws), ctypes.byref(nt), ctypes.byref(sm)),
+           "chessfad_ragged_plan_info")
+    return {"workspace_bytes": ws.value, "ntiles": nt.value, "smem_bytes": sm.value}
+
+
+def chessfad_ragged_plan_upload(plan, workspace, workspace_bytes, stream=None) -> int:
+    return load().chessfad_ragged_plan_upload(plan, _addr(workspace), workspace_bytes, _stream(stream))
+
+
+def chessfad_hvp_ragged(plan, xpack, vpack, outpack, params, workspace, workspace_bytes, stream=None) -> int:
+    p = ctypes.byref(params) if params is not None else None
+    return load().chessfad_hvp_ragged(plan, _addr(xpack), _addr(vpack), _addr(outpack), p, _addr(workspace),
+                                      workspace_bytes, _stream(stream))
+
+
+class RaggedPlan:
+    """Owns a plan and its device workspace (a torch uint8 tensor)."""
+
+    def __init__(self, reqs, prec=FP32_COMP, csize=0, device="cuda", stream=None):
+        import torch
+
+        self.prec = prec
+        self.handle = chessfad_ragged_plan_create(reqs, prec, csize)
+        info = chessfad_ragged_plan_info(self.handle)
+        self.info = info
+        self.workspace = torch.empty(max(256, info["workspace_bytes"]), dtype=torch.uint8, device=device)
+        _check(chessfad_ragged_plan_upload(self.handle, self.workspace, self.workspace.numel(), stream),
+               "chessfad_ragged_plan_upload")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def run(self, xpack, vpack, outpack, params=None, stream=None):
+        _check(chessfad_hvp_ragged(self.handle, xpack, vpack, outpack, params, self.workspace,
+                                   self.workspace.numel(), stream), "chessfad_hvp_ragged")
+        return outpack
+
+    def close(self):
+        if self.handle:
+            chessfad_ragged_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

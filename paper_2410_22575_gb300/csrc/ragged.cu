@@ -1,0 +1,345 @@
+// ragged.cu -- Hessian-vector products over an uneven batch: requests of
+// different test functions and different n in one persistent launch.
+//
+// Host side (a plan, built once per request table): requests are grouped by
+// (function, n); the point-major row space of each group is cut into tiles of
+// one CTA each (blockDim/tpr rows, the same (point, row, lane) decomposition as
+// the batched kernel, Sec. VI); tiles are sorted by estimated cost, largest
+// first, so the long Fletcher-Powell tiles at large n start early and the short
+// ones fill the tail.  The tables (tiles, request list, offsets) live in a
+// caller-provided device workspace together with a queue counter.
+//
+// Device side: a persistent kernel, a few CTAs per SM, whose CTAs take tile
+// after tile from the counter with atomicAdd and run the tile's sweeps.  No
+// CTA ever waits for another one.  A run is {memset of the counter, kernel},
+// both stream-ordered, so it can be captured into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "../../include/chessfad.h"
+#include "dispatch.h"
+
+namespace chessfad {
+
+struct RTile {
+    long long row0;     // first row of the tile in its group's row space
+    long long npoints;  // points (requests) in the group
+    int list0;          // group's first entry in the request list
+    int fn, n, nch, tpr, maxpts, mt;
+};
+
+constexpr int kRaggedBlock = 256;
+
+struct RaggedArgs {
+    const void *x;
+    const void *v;
+    void *out;
+    const double *A;
+    const double *B;
+    const double *Epack;
+    const RTile *tiles;
+    const int *list;
+    const long long *offs;
+    const long long *eoffs;
+    int *counter;
+    int ntiles;
+    int ld;
+};
+
+// The chunk sizes the uneven-batch kernel is built for; one persistent kernel
+// per (precision, chunk size) serves every function and every n.
+__host__ __device__ constexpr int ragged_mb(int C) { return C <= 8 ? 2 : 1; }
+
+template <typename T, int C, int FN>
+__device__ __forceinline__ void ragged_tile(const RaggedArgs &a, const RTile &t, unsigned char *smem)
+{
+    Job job;
+    job.x = a.x;
+    job.v = a.v;
+    job.out = a.out;
+    job.A = a.A;
+    job.B = a.B;
+    job.npoints = t.npoints;
+    job.row0 = t.row0;
+    job.n = t.n;
+    job.nch = t.nch;
+    job.tpr = t.tpr;
+    job.maxpts = t.maxpts;
+    job.mt = t.mt;
+    job.ld = a.ld;
+    ListPoints pm{a.list + t.list0, a.offs, a.eoffs, a.Epack};
+    if (IsComp<T>::value && t.n == 1) {
+        // One variable: FP64 sweep with float I/O (the Hessian is a single
+        // entry whose terms can cancel far below their size).
+        block_sweeps<double, float, 1, FN, true, 8>(job, pm, smem);
+    } else {
+        block_sweeps<T, T, C, FN, true, ragged_mb(C)>(job, pm, smem);
+    }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kRaggedBlock, sizeof(T) == 4 ? 2 : 1) ragged_kernel(const RaggedArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_tile;
+    for (;;) {
+        __syncthreads();  // the previous tile is done with shared memory and s_tile
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= a.ntiles) break;
+        const RTile tile = a.tiles[t];
+        switch (tile.fn) {
+        case FN_ROSENBROCK: ragged_tile<T, C, FN_ROSENBROCK>(a, tile, smem_raw); break;
+        case FN_ACKLEY: ragged_tile<T, C, FN_ACKLEY>(a, tile, smem_raw); break;
+        default: ragged_tile<T, C, FN_FP>(a, tile, smem_raw); break;
+        }
+    }
+}
+
+}  // namespace chessfad
+
+using namespace chessfad;
+
+struct chessfad_ragged_plan_s {
+    int prec = 0;
+    int csize = 0;
+    long long nreq = 0;
+    int max_fp_n = 0;
+    size_t smem = 0;
+    std::vector<RTile> tiles;
+    std::vector<int> list;
+    std::vector<long long> offs, eoffs;
+    // device workspace layout (bytes)
+    size_t off_counter = 0, off_tiles = 0, off_list = 0, off_offs = 0, off_eoffs = 0, total = 0;
+    std::vector<unsigned char> image;  // host image of the workspace tables
+    int grid_dev = -1, grid = 0;
+    double est_cost = 0.0;
+};
+
+namespace {
+
+size_t align256(size_t a) { return (a + 255) / 256 * 256; }
+
+int pow2_floor(int v)
+{
+    int p = 1;
+    while (p * 2 <= v) p *= 2;
+    return p;
+}
+
+// Relative cost of one sweep (FP32 instruction estimate of the dense rules).
+double sweep_cost(int fn, int n, int C)
+{
+    switch (fn) {
+    case CHESSFAD_ROSENBROCK: return (double)std::max(1, n - 1) * (22.0 * C + 11.0);
+    case CHESSFAD_ACKLEY: return (double)n * (9.0 * C + 5.0) + 15.0 * C;
+    default: return (double)n * n * (6.0 * C + 8.0) + (double)n * (11.0 * C);
+    }
+}
+
+int fp_tile_rows_ragged(int n, int prec, int mb)
+{
+    const size_t esz = (prec == CHESSFAD_FP64) ? 8 : 4;
+    int mt = (int)((48 * 1024) / (2 * (size_t)n * esz));
+    mt = std::max(8, mt / 8 * 8);
+    mt = std::min(mt, (n + 7) / 8 * 8);
+    if (mt % mb) mt = (mt / mb + 1) * mb;
+    return mt;
+}
+
+template <typename T, int C>
+cudaError_t launch_ragged(chessfad_ragged_plan_s *pl, const RaggedArgs &a, cudaStream_t stream)
+{
+    auto kern = ragged_kernel<T, C>;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (pl->grid_dev != dev) {
+        if (pl->smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+            if (e != cudaSuccess) return e;
+        }
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRaggedBlock, pl->smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        pl->grid = std::max(1, per_sm) * sms;
+        pl->grid_dev = dev;
+    }
+    if (a.ntiles == 0) return cudaSuccess;
+    e = cudaMemsetAsync(a.counter, 0, sizeof(int), stream);
+    if (e != cudaSuccess) return e;
+    kern<<<std::min(pl->grid, a.ntiles), kRaggedBlock, pl->smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, int prec, int csize,
+                                chessfad_ragged_plan *plan_out)
+{
+    if (!plan_out) return CHESSFAD_ERR_NULL;
+    *plan_out = nullptr;
+    if (nreq < 0) return CHESSFAD_ERR_BATCH;
+    if (nreq > 0 && !reqs) return CHESSFAD_ERR_NULL;
+    if (nreq > (1LL << 30)) return CHESSFAD_ERR_BATCH;
+    if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
+    if (csize == 0) csize = (prec == CHESSFAD_FP64) ? 8 : 8;
+    if (csize != 8 && csize != 16) return CHESSFAD_ERR_CHUNK;
+    for (long long q = 0; q < nreq; ++q) {
+        const chessfad_request &r = reqs[q];
+        if (r.fn < 0 || r.fn > 2) return CHESSFAD_ERR_FUNCTION;
+        if (r.n < 1 || r.n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
+        if (r.off < 0 || (r.fn == CHESSFAD_FLETCHER_POWELL && r.eoff < 0)) return CHESSFAD_ERR_PLAN;
+    }
+    auto *pl = new (std::nothrow) chessfad_ragged_plan_s();
+    if (!pl) return CHESSFAD_ERR_PLAN;
+    pl->prec = prec;
+    pl->csize = csize;
+    pl->nreq = nreq;
+
+    // Group by (fn, n); the request list holds each group's requests in order.
+    std::map<std::pair<int, int>, std::vector<int>> groups;
+    for (long long q = 0; q < nreq; ++q) groups[{reqs[q].fn, reqs[q].n}].push_back((int)q);
+    pl->offs.resize(nreq);
+    pl->eoffs.resize(nreq);
+    for (long long q = 0; q < nreq; ++q) {
+        pl->offs[q] = reqs[q].off;
+        pl->eoffs[q] = reqs[q].fn == CHESSFAD_FLETCHER_POWELL ? reqs[q].eoff : 0;
+    }
+    std::vector<std::pair<double, RTile>> work;
+    size_t smem = 0;
+    const int mb = ragged_mb(csize);
+    for (auto &g : groups) {
+        const int fn = g.first.first, n = g.first.second;
+        const int C = (prec == CHESSFAD_FP32_COMP && n == 1) ? 1 : csize;
+        const int nch = (n + C - 1) / C;
+        // Lanes per row: enough rows per tile to keep the per-point prologue
+        // small, more lanes only when a row's chunks are many.
+        const int tpr = std::min(32, pow2_floor(std::max(1, nch / 8)));
+        const int rows = kRaggedBlock / tpr;
+        const long long np = (long long)g.second.size();
+        const long long total_rows = np * n;
+        const int maxpts = (int)std::min<long long>(np, (rows - 1) / n + 2);
+        const int mt = (fn == CHESSFAD_FLETCHER_POWELL) ? fp_tile_rows_ragged(n, prec, (C == 1) ? 8 : mb) : 8;
+        if (fn == CHESSFAD_FLETCHER_POWELL) pl->max_fp_n = std::max(pl->max_fp_n, n);
+        const bool f64sweep = (prec == CHESSFAD_FP64) || n == 1;
+        const size_t bytes = f64sweep ? smem_layout<double>(fn, true, n, maxpts, mt).total
+                                      : smem_layout<float>(fn, true, n, maxpts, mt).total;
+        smem = std::max(smem, bytes);
+        const int list0 = (int)pl->list.size();
+        for (int q : g.second) pl->list.push_back(q);
+        const double per_row = nch * sweep_cost(fn, n, C);
+        for (long long r0 = 0; r0 < total_rows; r0 += rows) {
+            RTile t{};
+            t.row0 = r0;
+            t.npoints = np;
+            t.list0 = list0;
+            t.fn = fn;
+            t.n = n;
+            t.nch = nch;
+            t.tpr = tpr;
+            t.maxpts = maxpts;
+            t.mt = mt;
+            const double cost = per_row * (double)std::min<long long>(rows, total_rows - r0) + 2000.0;
+            work.push_back({cost, t});
+            pl->est_cost += cost;
+        }
+    }
+    std::stable_sort(work.begin(), work.end(),
+                     [](const std::pair<double, RTile> &a, const std::pair<double, RTile> &b) { return a.first > b.first; });
+    pl->tiles.reserve(work.size());
+    for (auto &w : work) pl->tiles.push_back(w.second);
+    pl->smem = smem;
+
+    // Workspace: counter | tiles | list | offs | eoffs.
+    pl->off_counter = 0;
+    pl->off_tiles = align256(sizeof(int));
+    pl->off_list = align256(pl->off_tiles + pl->tiles.size() * sizeof(RTile));
+    pl->off_offs = align256(pl->off_list + pl->list.size() * sizeof(int));
+    pl->off_eoffs = align256(pl->off_offs + pl->offs.size() * sizeof(long long));
+    pl->total = align256(pl->off_eoffs + pl->eoffs.size() * sizeof(long long));
+    pl->image.assign(pl->total, 0);
+    if (!pl->tiles.empty()) std::memcpy(&pl->image[pl->off_tiles], pl->tiles.data(), pl->tiles.size() * sizeof(RTile));
+    if (!pl->list.empty()) std::memcpy(&pl->image[pl->off_list], pl->list.data(), pl->list.size() * sizeof(int));
+    if (!pl->offs.empty()) std::memcpy(&pl->image[pl->off_offs], pl->offs.data(), pl->offs.size() * sizeof(long long));
+    if (!pl->eoffs.empty())
+        std::memcpy(&pl->image[pl->off_eoffs], pl->eoffs.data(), pl->eoffs.size() * sizeof(long long));
+    *plan_out = pl;
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_ragged_plan_destroy(chessfad_ragged_plan plan)
+{
+    delete plan;
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes, long long *ntiles,
+                              size_t *smem_bytes)
+{
+    if (!plan) return CHESSFAD_ERR_PLAN;
+    if (workspace_bytes) *workspace_bytes = plan->total;
+    if (ntiles) *ntiles = (long long)plan->tiles.size();
+    if (smem_bytes) *smem_bytes = plan->smem;
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_ragged_plan_upload(chessfad_ragged_plan plan, void *workspace, size_t workspace_bytes,
+                                chessfad_stream_t stream)
+{
+    if (!plan) return CHESSFAD_ERR_PLAN;
+    if (!workspace || workspace_bytes < plan->total) return CHESSFAD_ERR_WORKSPACE;
+    if (plan->total == 0) return CHESSFAD_SUCCESS;
+    cudaError_t e = cudaMemcpyAsync(workspace, plan->image.data(), plan->total, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+}
+
+int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpack, const void *vpack, void *outpack,
+                        const chessfad_fp_params *params, void *workspace, size_t workspace_bytes,
+                        chessfad_stream_t stream)
+{
+    if (!plan) return CHESSFAD_ERR_PLAN;
+    if (!workspace || workspace_bytes < plan->total) return CHESSFAD_ERR_WORKSPACE;
+    if (plan->tiles.empty()) return CHESSFAD_SUCCESS;
+    if (!xpack || !vpack || !outpack) return CHESSFAD_ERR_NULL;
+    if (plan->max_fp_n > 0 && (!params || !params->A || !params->B || !params->E || params->ld < plan->max_fp_n))
+        return CHESSFAD_ERR_PARAMS;
+    unsigned char *ws = static_cast<unsigned char *>(workspace);
+    RaggedArgs a{};
+    a.x = xpack;
+    a.v = vpack;
+    a.out = outpack;
+    if (params) {
+        a.A = params->A;
+        a.B = params->B;
+        a.Epack = params->E;
+        a.ld = params->ld;
+    }
+    a.tiles = reinterpret_cast<const RTile *>(ws + plan->off_tiles);
+    a.list = reinterpret_cast<const int *>(ws + plan->off_list);
+    a.offs = reinterpret_cast<const long long *>(ws + plan->off_offs);
+    a.eoffs = reinterpret_cast<const long long *>(ws + plan->off_eoffs);
+    a.counter = reinterpret_cast<int *>(ws + plan->off_counter);
+    a.ntiles = (int)plan->tiles.size();
+    cudaError_t e;
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (plan->prec == CHESSFAD_FP64)
+        e = plan->csize == 16 ? launch_ragged<double, 16>(plan, a, s) : launch_ragged<double, 8>(plan, a, s);
+    else
+        e = plan->csize == 16 ? launch_ragged<float, 16>(plan, a, s) : launch_ragged<float, 8>(plan, a, s);
+    return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+}
+
+}  // extern "C"

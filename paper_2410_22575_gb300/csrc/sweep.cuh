@@ -248,34 +248,71 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const
     return f;
 }
 
-// ------------------------------------------------------------------ kernel
+// ------------------------------------------------------------------ block work
+// A block-uniform unit of work: the rows [row0, row0 + blockDim/tpr) of a
+// point-major row space (row = point * n + i) over `npoints` points of one
+// function and one n.  Point addressing is a policy: a contiguous batch, or a
+// list of requests with their own offsets (the uneven batch).
+struct Job {
+    const void *x;
+    const void *v;
+    void *out;
+    const double *A;
+    const double *B;
+    long long npoints;
+    long long row0;
+    int n, nch, tpr, maxpts, mt, ld;
+};
+
+// Points p = 0 .. batch-1 of a [batch][n] array; one E for all points.
+struct ContigPoints {
+    const double *E;
+    int n;
+    __device__ __forceinline__ long long off(long long p) const { return p * n; }
+    __device__ __forceinline__ const double *e(long long) const { return E; }
+};
+
+// Point p of a request group is request list[p]; its x, v, out start at
+// off[list[p]] and its Fletcher-Powell E at Epack + eoff[list[p]].
+struct ListPoints {
+    const int *list;
+    const long long *offs;
+    const long long *eoffs;
+    const double *Epack;
+    __device__ __forceinline__ long long off(long long p) const { return offs[list[p]]; }
+    __device__ __forceinline__ const double *e(long long p) const { return Epack + eoffs[list[p]]; }
+};
+
 // T is the arithmetic type of the sweep, IO the element type of x, v and the
 // output (IO = T except for the one-variable compensated-FP32 case, which
-// computes in FP64 with float I/O).
-template <typename T, typename IO, int C, int FN, bool HVP, int MB>
-__global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
+// computes in FP64 with float I/O).  Every thread of the block must call it
+// (it synchronises the block).
+template <typename T, typename IO, int C, int FN, bool HVP, int MB, typename PM>
+__device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n;
     const Smem<T> L = smem_layout<T>(FN, HVP, n, a.maxpts, a.mt);
     T *xs = reinterpret_cast<T *>(smem_raw + L.xs);
     T *vs = reinterpret_cast<T *>(smem_raw + L.vs);
 
-    const long long t0 = (long long)blockIdx.x * blockDim.x;
-    const long long p0 = t0 / a.tpp;
-    long long plast = (t0 + blockDim.x - 1) / a.tpp;
-    if (plast > a.batch - 1) plast = a.batch - 1;
+    const int rows_per_block = blockDim.x / a.tpr;
+    const long long p0 = a.row0 / n;
+    long long plast = (a.row0 + rows_per_block - 1) / n;
+    if (plast > a.npoints - 1) plast = a.npoints - 1;
     const int npts = (int)(plast - p0 + 1);
     const int tid = threadIdx.x;
 
-    // ---- stage x (and v) of this block's points: one contiguous range.
+    // ---- stage x (and v) of this block's points (n contiguous values each;
+    // one contiguous range for a contiguous batch).
     {
-        const IO *X = reinterpret_cast<const IO *>(a.x) + p0 * n;
-        const IO *V = reinterpret_cast<const IO *>(a.v) + p0 * n;
+        const IO *X = reinterpret_cast<const IO *>(a.x);
+        const IO *V = reinterpret_cast<const IO *>(a.v);
         const int cnt = npts * n;
         for (int e = tid; e < cnt; e += blockDim.x) {
-            xs[e] = (T)X[e];
-            if (HVP) vs[e] = (T)V[e];
+            const int q = e / n, k = e - q * n;
+            const long long o = pm.off(p0 + q) + k;
+            xs[e] = (T)X[o];
+            if (HVP) vs[e] = (T)V[o];
         }
     }
     __syncthreads();
@@ -359,18 +396,17 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
             const double *cq = dc + q * n;
             double s = 0.0;
             for (int j = 0; j < n; ++j) s = fma(Ar[j], sq[j], fma(Br[j], cq[j], s));
-            res[e] = (T)(a.E[m] - s);
+            res[e] = (T)(pm.e(p0 + q)[m] - s);
         }
         __syncthreads();
     }
 
     // ---- this thread's (point, row, lane)
-    const long long gid = t0 + tid;
-    const long long p = gid / a.tpp;
-    const int rem = (int)(gid - p * a.tpp);
-    const int i = rem / a.tpr;
-    const int r = rem - i * a.tpr;
-    const bool active = p < a.batch;
+    const long long row = a.row0 + tid / a.tpr;
+    const int r = tid % a.tpr;
+    const long long p = row / n;
+    const int i = (int)(row - p * n);
+    const bool active = p < a.npoints;
     const int q = active ? (int)(p - p0) : 0;
     const T *xq = xs + q * n;
     const T *vq = vs + q * n;
@@ -395,7 +431,7 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
             }
         } else {
             if (active) {
-                IO *H = reinterpret_cast<IO *>(a.out) + ((size_t)p * n + i) * n;
+                IO *H = reinterpret_cast<IO *>(a.out) + (pm.off(p) + i) * n;
 #pragma unroll
                 for (int l = 0; l < C; ++l)
                     if (cstart + l < n) H[cstart + l] = (IO)f.h[l];
@@ -487,6 +523,7 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
 
     if constexpr (HVP) {
         // Sum the tpr lanes of the row (aligned groups inside one warp).
+        IO *O = reinterpret_cast<IO *>(a.out);
         if constexpr (IsComp<T>::value) {
             for (int off = a.tpr >> 1; off > 0; off >>= 1) {
                 CSum o;
@@ -494,12 +531,37 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
                 o.e = __shfl_xor_sync(0xffffffffu, dot.e, off);
                 dot = csum_merge(dot, o);
             }
-            if (active && r == 0) reinterpret_cast<float *>(a.out)[(size_t)p * n + i] = csum_value(dot);
+            if (active && r == 0) O[pm.off(p) + i] = (IO)csum_value(dot);
         } else {
             for (int off = a.tpr >> 1; off > 0; off >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, off);
-            if (active && r == 0) reinterpret_cast<IO *>(a.out)[(size_t)p * n + i] = (IO)dot;
+            if (active && r == 0) O[pm.off(p) + i] = (IO)dot;
         }
     }
+}
+
+// ------------------------------------------------------------------ kernel
+// One launch over a contiguous batch: block b handles rows
+// [b * blockDim/tpr, (b+1) * blockDim/tpr) of the batch's row space.
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+__global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Job job;
+    job.x = a.x;
+    job.v = a.v;
+    job.out = a.out;
+    job.A = a.A;
+    job.B = a.B;
+    job.npoints = a.batch;
+    job.row0 = (long long)blockIdx.x * (blockDim.x / a.tpr);
+    job.n = a.n;
+    job.nch = a.nch;
+    job.tpr = a.tpr;
+    job.maxpts = a.maxpts;
+    job.mt = a.mt;
+    job.ld = a.ld;
+    ContigPoints pm{a.E, a.n};
+    block_sweeps<T, IO, C, FN, HVP, MB>(job, pm, smem_raw);
 }
 
 // Host-side launch helper: computes the layout, opts into large dynamic

@@ -1,0 +1,123 @@
+"""The uneven batch (requests of three functions and n in [1, 512] in one
+persistent launch) against the FP64 oracle, request by request, and its
+CUDA-graph capture."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2410_22575_gb300 as cf
+from paper_2410_22575_gb300 import metrics, workloads as W
+
+from gpu_helpers import BOUND
+
+pytestmark = pytest.mark.gpu
+
+
+class DevRagged:
+    def __init__(self, rg: W.Ragged, prec, csize=0):
+        import torch
+
+        self.rg = rg
+        self.prec = prec
+        dt = torch.float64 if prec == cf.FP64 else torch.float32
+        self.x = torch.tensor(rg.xpack, dtype=dt, device="cuda")
+        self.v = torch.tensor(rg.vpack, dtype=dt, device="cuda")
+        self.out = torch.full_like(self.x, float("nan"))
+        self.xh = self.x.double().cpu().numpy()
+        self.vh = self.v.double().cpu().numpy()
+        self.A = torch.tensor(rg.fp.A, device="cuda")
+        self.B = torch.tensor(rg.fp.B, device="cuda")
+        self.E = torch.tensor(rg.Epack, device="cuda")
+        self.params = cf.fp_params(self.A, self.B, self.E)
+        self.plan = cf.RaggedPlan(cf.requests(rg.fns, rg.ns, rg.offs, rg.eoffs), prec, csize)
+
+    def run(self, stream=None):
+        import torch
+
+        self.plan.run(self.x, self.v, self.out, self.params, stream)
+        torch.cuda.synchronize()
+        return self.out.double().cpu().numpy()
+
+    def errors(self, out, idx=None):
+        rg = self.rg
+        if idx is None:
+            idx = np.arange(rg.nreq)
+        sub = rg.subset(idx)
+        xs = np.concatenate([self.xh[rg.offs[q]:rg.offs[q] + rg.ns[q]] for q in idx])
+        vs = np.concatenate([self.vh[rg.offs[q]:rg.offs[q] + rg.ns[q]] for q in idx])
+        got = np.concatenate([out[rg.offs[q]:rg.offs[q] + rg.ns[q]] for q in idx])
+        ref, hn = oracle.hvp_ragged(sub.fns, sub.ns, sub.offs, sub.eoffs, xs, vs, rg.fp.A, rg.fp.B, rg.Epack, rg.ld)
+        return metrics.ragged_hvp_errors(got, ref, hn, vs, sub.ns, sub.offs)
+
+
+@pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
+@pytest.mark.parametrize("csize", [8, 16])
+def test_small_uneven_batch(prec, csize):
+    rg = W.make_ragged(nreq=400, seed=9, nmax=80)
+    d = DevRagged(rg, prec, csize)
+    out = d.run()
+    assert np.all(np.isfinite(out))
+    e = d.errors(out)
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+
+
+def test_one_variable_and_mixed_requests():
+    rg = W.make_ragged(nreq=300, seed=21, nmax=12)
+    # force some one-variable requests
+    fns = rg.fns.copy()
+    ns = rg.ns.copy()
+    ns[::7] = 1
+    offs = np.zeros(len(ns), dtype=np.int64)
+    offs[1:] = np.cumsum(ns[:-1])
+    rng = np.random.Generator(np.random.PCG64(2))
+    xp = np.concatenate([rng.uniform(*W.X_RANGE[int(f)], int(n)) for f, n in zip(fns, ns)])
+    vp = rng.uniform(-1, 1, int(ns.sum()))
+    eoffs = np.array([rg.e_of_n.get(int(n), 0) if f == W.FLETCHER_POWELL else 0 for f, n in zip(fns, ns)])
+    # E for every FP size present (including 1)
+    Epack, e_of_n, pos = [], {}, 0
+    for n in sorted(set(int(n) for f, n in zip(fns, ns) if f == W.FLETCHER_POWELL)):
+        e = W.fp_rhs(rg.fp.A[:n, :n], rg.fp.B[:n, :n], rg.fp.alpha[:n])
+        e_of_n[n] = pos
+        Epack.append(e)
+        pos += n
+    eoffs = np.array([e_of_n.get(int(n), 0) if f == W.FLETCHER_POWELL else 0 for f, n in zip(fns, ns)])
+    rg2 = W.Ragged(fns, ns, offs, xp, vp, rg.fp, np.concatenate(Epack), eoffs, e_of_n)
+    for prec in (cf.FP64, cf.FP32_COMP):
+        d = DevRagged(rg2, prec)
+        e = d.errors(d.run())
+        assert e.max() <= BOUND[prec], (prec, e.max())
+
+
+def test_graph_capture_and_replay_are_deterministic():
+    import torch
+
+    rg = W.make_ragged(nreq=500, seed=3, nmax=64)
+    d = DevRagged(rg, cf.FP32_COMP)
+    direct = d.run()  # also performs the one-time per-device set-up
+    d.out.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        d.plan.run(d.x, d.v, d.out, d.params)
+    for _ in range(2):
+        d.out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(d.out.double().cpu().numpy(), direct)
+    e = d.errors(direct)
+    assert e.max() <= BOUND[cf.FP32_COMP]
+
+
+def test_full_ragged_workload_sampled():
+    """All 100000 requests in one persistent launch (compensated FP32); a
+    sample of 600 requests, including the 60 most expensive, is compared with
+    the oracle, and every output is finite."""
+    rg = W.make_ragged()
+    d = DevRagged(rg, cf.FP32_COMP)
+    out = d.run()
+    assert np.all(np.isfinite(out))
+    cost = np.where(rg.fns == W.FLETCHER_POWELL, rg.ns.astype(float) ** 4, rg.ns.astype(float) ** 3)
+    big = np.argsort(-cost)[:60]
+    rnd = np.random.Generator(np.random.PCG64(0)).choice(rg.nreq, 540, replace=False)
+    idx = np.unique(np.concatenate([big, rnd]))
+    e = d.errors(out, idx)
+    assert e.max() <= BOUND[cf.FP32_COMP], (e.max(), np.median(e))
