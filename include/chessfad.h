@@ -213,6 +213,29 @@ CHESSFAD_API int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpac
                                      const chessfad_fp_params *params, void *workspace, size_t workspace_bytes,
                                      chessfad_stream_t stream);
 
+/* No-allocation variant of chessfad_hvp_ragged, for callers that cannot call
+ * cudaMalloc: a host framework that owns device memory through its own pool,
+ * a plugin or callback that must not allocate or implicitly synchronise the
+ * device, or real-time code with no room for allocation latency.  The paper
+ * has no counterpart; it is a deployment convenience.
+ *
+ * The scratch (the plan's tables and the queue counter) lives in a static
+ * device array of CHESSFAD_RAGGED_STATIC_BYTES that every GPU which loads the
+ * library holds until the process exits.  Each call copies the plan's tables
+ * and a zeroed counter into it (cudaMemcpyAsync on stream) and launches the
+ * persistent kernel; it allocates nothing and calls no allocating routine.
+ * The first call on a device also looks up the array's device address on
+ * that device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array, so calls whose work overlaps on
+ * the GPU (other streams, other host threads) race; serialise them.
+ * Returns CHESSFAD_ERR_WORKSPACE if the plan's tables exceed
+ * CHESSFAD_RAGGED_STATIC_BYTES (chessfad_ragged_plan_info reports the
+ * size); other arguments and errors as chessfad_hvp_ragged. */
+#define CHESSFAD_RAGGED_STATIC_BYTES (8u << 20)
+CHESSFAD_API int chessfad_hvp_ragged_noalloc(chessfad_ragged_plan plan, const void *xpack, const void *vpack,
+                                             void *outpack, const chessfad_fp_params *params,
+                                             chessfad_stream_t stream);
+
 /* Registers per thread and local-memory (spill) bytes per thread of the
  * HVP (hvp != 0) or Hessian kernel for (fn, prec, csize), as compiled for
  * the current device.  Host only; launches nothing. */

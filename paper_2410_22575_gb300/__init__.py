@@ -80,6 +80,8 @@ def load(build_if_missing: bool = True):
                                                   ctypes.POINTER(ctypes.c_size_t)]
         lib.chessfad_ragged_plan_upload.argtypes = [P, P, ctypes.c_size_t, P]
         lib.chessfad_hvp_ragged.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
+        lib.chessfad_hvp_ragged_noalloc.argtypes = [P, P, P, P, P, P]
+        lib.chessfad_hvp_ragged_noalloc.restype = I
         lib.chessfad_strerror.argtypes = [I]
         lib.chessfad_strerror.restype = ctypes.c_char_p
         lib.chessfad_version.argtypes = []
@@ -280,6 +282,13 @@ def chessfad_hvp_ragged(plan, xpack, vpack, outpack, params, workspace, workspac
     p = ctypes.byref(params) if params is not None else None
     return load().chessfad_hvp_ragged(plan, _addr(xpack), _addr(vpack), _addr(outpack), p, _addr(workspace),
                                       workspace_bytes, _stream(stream))
+
+
+def chessfad_hvp_ragged_noalloc(plan, xpack, vpack, outpack, params=None, stream=None) -> int:
+    """chessfad_hvp_ragged without a caller workspace: the scratch is the
+    library's static device array (see include/chessfad.h)."""
+    p = ctypes.byref(params) if params is not None else None
+    return load().chessfad_hvp_ragged_noalloc(plan, _addr(xpack), _addr(vpack), _addr(outpack), p, _stream(stream))
 
 
 class RaggedPlan:

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -343,3 +344,88 @@ int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpack, const void
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation entry point.
+//
+// Some callers cannot call cudaMalloc: a host framework that owns device
+// memory through its own pool (raw allocations would bypass its accounting or
+// fail because the pool holds the memory), a plugin or callback that must not
+// allocate or implicitly synchronise the device (cudaMalloc may do both), or
+// real-time code for which allocation latency is unbounded.  For them the
+// uneven-batch run keeps its scratch -- the queue counter and the plan's
+// tables -- in a file-scope __device__ array of CHESSFAD_RAGGED_STATIC_BYTES
+// that every GPU which loads this library holds until the process exits.
+//
+// In host code the array's name is only a host-side stand-in; its device
+// address is taken once per device with cudaGetSymbolAddress, with that device
+// current, the first time the entry point runs on it.  Every call shares the
+// array: each call copies the plan's tables and a zeroed counter into it
+// (stream-ordered) before its kernel, so calls whose work overlaps on the GPU
+// race on the shared scratch.
+static __device__ __align__(256) unsigned char g_ragged_scratch[CHESSFAD_RAGGED_STATIC_BYTES];
+
+namespace {
+
+constexpr int kMaxScratchDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxScratchDevices] = {};
+
+int ragged_scratch_address(void **addr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxScratchDevices) return CHESSFAD_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ragged_scratch) != cudaSuccess || !p) return CHESSFAD_ERR_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *addr = g_scratch_addr[dev];
+    return CHESSFAD_SUCCESS;
+}
+
+}  // namespace
+
+extern "C" int chessfad_hvp_ragged_noalloc(chessfad_ragged_plan plan, const void *xpack, const void *vpack,
+                                           void *outpack, const chessfad_fp_params *params,
+                                           chessfad_stream_t stream)
+{
+    if (!plan) return CHESSFAD_ERR_PLAN;
+    if (plan->total > (size_t)CHESSFAD_RAGGED_STATIC_BYTES) return CHESSFAD_ERR_WORKSPACE;
+    if (plan->tiles.empty()) return CHESSFAD_SUCCESS;
+    if (!xpack || !vpack || !outpack) return CHESSFAD_ERR_NULL;
+    if (plan->max_fp_n > 0 && (!params || !params->A || !params->B || !params->E || params->ld < plan->max_fp_n))
+        return CHESSFAD_ERR_PARAMS;
+    void *scratch = nullptr;
+    int st = ragged_scratch_address(&scratch);
+    if (st != CHESSFAD_SUCCESS) return st;
+    const cudaStream_t s = (cudaStream_t)stream;
+    // The plan's image holds the tables and a zero queue counter.
+    if (cudaMemcpyAsync(scratch, plan->image.data(), plan->total, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CHESSFAD_ERR_CUDA;
+    unsigned char *ws = static_cast<unsigned char *>(scratch);
+    RaggedArgs a{};
+    a.x = xpack;
+    a.v = vpack;
+    a.out = outpack;
+    if (params) {
+        a.A = params->A;
+        a.B = params->B;
+        a.Epack = params->E;
+        a.ld = params->ld;
+    }
+    a.tiles = reinterpret_cast<const RTile *>(ws + plan->off_tiles);
+    a.list = reinterpret_cast<const int *>(ws + plan->off_list);
+    a.offs = reinterpret_cast<const long long *>(ws + plan->off_offs);
+    a.eoffs = reinterpret_cast<const long long *>(ws + plan->off_eoffs);
+    a.counter = reinterpret_cast<int *>(ws + plan->off_counter);
+    a.ntiles = (int)plan->tiles.size();
+    cudaError_t e;
+    if (plan->prec == CHESSFAD_FP64)
+        e = plan->csize == 16 ? launch_ragged<double, 16>(plan, a, s) : launch_ragged<double, 8>(plan, a, s);
+    else
+        e = plan->csize == 16 ? launch_ragged<float, 16>(plan, a, s) : launch_ragged<float, 8>(plan, a, s);
+    return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+}
