@@ -45,20 +45,34 @@ SM_MAX_MHZ = 2070.0
 FP64_LANES_PER_SM = 2
 
 
-def model_flops_ackley(n: int, c: int) -> float:
-    """Model flops of one Ackley HVP by the dense chunked-hDual method (the
-    Sec. V operation model extended to Ackley's op list; FMA = 2):
-    n*nch*[n(20c+12) + 22c+18] + 2n^2."""
+def sym_items(n: int, c: int) -> int:
+    """Evaluations of f per point by the symmetric method (Alg. 6 / Alg. 8):
+    rows i with the chunks from their diagonal chunk on, n(n/c+1)/2 when c
+    divides n (Sec. V)."""
     nch = -(-n // c)
-    return n * nch * (n * (20 * c + 12) + 22 * c + 18) + 2 * n * n
+    return sum(min(c, n - R * c) * (nch - R) for R in range(nch))
+
+
+def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
+    """Model flops of one Ackley HVP by the dense chunked-hDual method (the
+    Sec. V operation model extended to Ackley's op list; FMA = 2): per
+    evaluation of f, n(20c+12) + 22c+18; n*nch evaluations (plain, Alg. 7) or
+    sym_items(n, c) (symmetric, Alg. 8); plus 2n^2 for the row dots."""
+    nch = -(-n // c)
+    sweeps = sym_items(n, c) if symmetric else n * nch
+    return sweeps * (n * (20 * c + 12) + 22 * c + 18) + 2 * n * n
+
+
+# Sources that define the headline sweep kernel (the ncu traffic figure is
+# reported only while these are unchanged since the capture).
+KERNEL_SOURCES = ("hdual.cuh", "sweep.cuh", "dispatch.h", "k_ackley_f32c.cu")
 
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -215,19 +229,21 @@ def gpu_arm(args):
         sweep = {}
         for c in (4, 8, 16, 32):
             info = cf.chessfad_kernel_info(fn, prec, c, True)
-            if info["local_bytes"] > 0:
+            if info["local_bytes"] > 48:
                 sweep[str(c)] = {"skipped": "spills registers", **info}
                 continue
+            ent = dict(info)
+            for mname, ccfg in (("plain", cf.Config(c, 1, 256)), ("symmetric", cf.Config(c, 0, 0, cf.SYMMETRIC, 64))):
+                def stc(ccfg=ccfg):
+                    st = cf.chessfad_hvp_config(fn, n, batch, ccfg, x, v, out, None, prec, stream)
+                    if st != 0:
+                        raise cf.ChessfadError(st, "chessfad_hvp")
 
-            def stc(c=c):
-                st = cf.chessfad_hvp(fn, n, batch, c, x, v, out, None, prec, stream)
-                if st != 0:
-                    raise cf.ChessfadError(st, "chessfad_hvp")
-
-            k = max(1, min(5, steps))
-            m = timed_steps(stc, k, 1, stream, flush)
-            t = max_over_ranks(world, sum(m), dev) / k
-            sweep[str(c)] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t, **info}
+                k = max(1, min(5, steps))
+                m = timed_steps(stc, k, 1, stream, flush)
+                t = max_over_ranks(world, sum(m), dev) / k
+                ent[mname] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t}
+            sweep[str(c)] = ent
         res[prec]["sweep"] = sweep
         del x, v, out
 
@@ -253,6 +269,8 @@ def gpu_arm(args):
     barrier(world)
     tot_e2e = max_over_ranks(world, sum(ms_e2e), dev)
 
+    ragged = None if args.no_ragged else ragged_arm(args, world, dev, stream, flush)
+
     if rank != 0:
         if world > 1:
             import torch.distributed as dist
@@ -265,7 +283,8 @@ def gpu_arm(args):
     value = world * batch * f32["steps"] / (f32["total_ms"] * 1e-3)
     v64 = world * batch * f64["steps"] / (f64["total_ms"] * 1e-3)
     c = f32["cfg"]["csize"]
-    flops_launch = model_flops_ackley(n, c) * batch
+    sym32 = f32["cfg"]["method"] == "symmetric"
+    flops_launch = model_flops_ackley(n, c, sym32) * batch
     avg_ms = sum(f32["ms"]) / len(f32["ms"])
     peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
     peak_fp64 = SM_COUNT * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
@@ -280,10 +299,11 @@ def gpu_arm(args):
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         tj = json.load(open(tfile))
-        ent = tj.get(f"{WORKLOAD}/fp32_comp/c{c}")
+        ent = tj.get(f"{WORKLOAD}/fp32_comp/{f32['cfg']['method']}/c{c}")
         if ent and ent.get("source_hash") == kernel_source_hash():
             traffic = ent.get("dram_bytes_per_launch")
     c64 = f64["cfg"]["csize"]
+    sym64 = f64["cfg"]["method"] == "symmetric"
     line = {
         "metric": METRIC,
         "value": value,
@@ -302,13 +322,14 @@ def gpu_arm(args):
                    "parallelism": f"replicas x{world} (points independent, no collective)"},
         "fp64": {"value": v64, "unit": "HVP/s", "steps": f64["steps"], "ms_per_step": f64["total_ms"] / f64["steps"],
                  **{k: v for k, v in f64["cfg"].items()},
-                 "model_tflops": model_flops_ackley(n, c64) * batch / (f64["total_ms"] / f64["steps"] * 1e-3) / 1e12,
+                 "model_tflops": model_flops_ackley(n, c64, sym64) * batch / (f64["total_ms"] / f64["steps"] * 1e-3) / 1e12,
                  "peak_tflops_derived": peak_fp64 / 1e12},
         "fp32_over_fp64": value / v64,
         "chunk_sweep": {"fp32_comp": f32["sweep"], "fp64": f64["sweep"]},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak_fp32, "traffic": traffic,
-                     "flops_per_launch": flops_launch, "kernel": "sweep_kernel<float,%d,ACKLEY,HVP>" % c,
+                     "flops_per_launch": flops_launch,
+                     "kernel": ("sym_kernel<float,%d,ACKLEY,HVP>" if sym32 else "sweep_kernel<float,%d,ACKLEY,HVP>") % c,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "peak_microbench": None if micro32 is None else micro32 / 1e12,
                      "frac_of_microbench": None if micro32 is None else achieved / micro32,
@@ -318,9 +339,87 @@ def gpu_arm(args):
         "gpu_launches": f32["steps"],
         "clocks": f32.get("clocks"),
     }
+    if ragged is not None:
+        line["ragged_100k"] = {k: v for k, v in ragged.items() if not k.startswith("_")}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(b, c, f32, f64, args)
+        if ragged is not None:
+            line["ragged_100k"]["error_vs_oracle_sample"] = ragged_error(ragged)
     print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ uneven batch
+def model_flops_request(fn: int, n: int, c: int) -> float:
+    """Model flops of one HVP by the dense chunked-hDual method (FMA = 2)."""
+    nch = -(-n // c)
+    if fn == 0:
+        return n * nch * max(0, n - 1) * (38 * c + 21) + 2 * n * n
+    if fn == 1:
+        return model_flops_ackley(n, c)
+    return n * nch * (8 * n * n * (c + 1) + n * (20 * c + 11)) + 2 * n * n
+
+
+def ragged_arm(args, world, dev, stream, flush):
+    """The 100000-request uneven batch (three functions, n log-uniform in
+    [2, 512], seed 4) in compensated FP32: one persistent launch per step,
+    replayed from a captured CUDA graph."""
+    import numpy as np
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    rg = W.make_ragged()
+    c = 8
+    reqs = cf.requests(rg.fns, rg.ns, rg.offs, rg.eoffs)
+    t0 = time.perf_counter()
+    plan = cf.RaggedPlan(reqs, cf.FP32_COMP, c)
+    t_plan = time.perf_counter() - t0
+    x = torch.tensor(rg.xpack, dtype=torch.float32, device=dev)
+    v = torch.tensor(rg.vpack, dtype=torch.float32, device=dev)
+    out = torch.empty_like(x)
+    A = torch.tensor(rg.fp.A, device=dev)
+    B = torch.tensor(rg.fp.B, device=dev)
+    E = torch.tensor(rg.Epack, device=dev)
+    params = cf.fp_params(A, B, E)
+    plan.run(x, v, out, params)  # per-device set-up, outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run(x, v, out, params)
+    barrier(world)
+    ms = timed_steps(g.replay, args.ragged_steps, 0, stream, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    tot = max_over_ranks(world, sum(ms), dev)
+    flops = sum(model_flops_request(int(f), int(n), c) for f, n in zip(rg.fns, rg.ns))
+    per = tot / len(ms)
+    return {"value": world * rg.nreq * len(ms) / (tot * 1e-3), "unit": "HVP/s", "requests": rg.nreq,
+            "steps": len(ms), "warmup": 1, "ms_per_step": per, "precision": "fp32_comp", "csize": c,
+            "launch": "one persistent kernel per step, CUDA graph replay", "tiles": plan.info["ntiles"],
+            "workspace_bytes": plan.info["workspace_bytes"], "plan_seconds": t_plan,
+            "model_tflops": flops / (per * 1e-3) / 1e12,
+            "_out": out, "_x": x, "_v": v, "_rg": rg}
+
+
+def ragged_error(r):
+    """Oracle check of 200 requests of the uneven batch (cpu_baseline leg)."""
+    import numpy as np
+
+    import oracle
+    from paper_2410_22575_gb300 import metrics
+
+    rg = r["_rg"]
+    idx = np.sort(np.random.Generator(np.random.PCG64(0)).choice(rg.nreq, 200, replace=False))
+    sub = rg.subset(idx)
+    xh = r["_x"].double().cpu().numpy()
+    vh = r["_v"].double().cpu().numpy()
+    oh = r["_out"].double().cpu().numpy()
+    take = lambda a: np.concatenate([a[rg.offs[q]:rg.offs[q] + rg.ns[q]] for q in idx])
+    xs, vs, got = take(xh), take(vh), take(oh)
+    ref, hn = oracle.hvp_ragged(sub.fns, sub.ns, sub.offs, sub.eoffs, xs, vs, rg.fp.A, rg.fp.B, rg.Epack, rg.ld)
+    e = metrics.ragged_hvp_errors(got, ref, hn, vs, sub.ns, sub.offs)
+    return {**metrics.summary(e), "requests": len(idx)}
 
 
 # ------------------------------------------------------------------ CPU oracle
@@ -407,7 +506,10 @@ def kernel_only(args):
     import paper_2410_22575_gb300 as cf
     from paper_2410_22575_gb300 import workloads as W
 
-    b = W.workload(args.workload, batch=args.batch)
+    if args.fn is not None:
+        b = W.make_batch(args.fn, args.n, args.batch or 1024, args.seed)
+    else:
+        b = W.workload(args.workload, batch=args.batch)
     prec = cf.FP64 if args.prec == "fp64" else cf.FP32_COMP
     dt = torch.float64 if prec == cf.FP64 else torch.float32
     x = torch.tensor(b.x, dtype=dt, device="cuda")
@@ -417,7 +519,10 @@ def kernel_only(args):
     if b.fn == W.FLETCHER_POWELL:
         keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
         params = cf.fp_params(*keep)
-    cfg = cf.Config(args.csize, args.tpr, args.block)
+    if args.method == "symmetric":
+        cfg = cf.Config(args.csize, 0, 0, cf.SYMMETRIC, args.tpp)
+    else:
+        cfg = cf.Config(args.csize, args.tpr, args.block)
     stream = torch.cuda.current_stream()
     ms = []
     for k in range(args.warmup + args.steps):
@@ -444,13 +549,20 @@ def main():
     ap.add_argument("--impl", choices=["chessfad", "reference"], default="chessfad")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the 100000-request uneven batch")
+    ap.add_argument("--ragged-steps", type=int, default=1)
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fn", type=int, default=None, help="kernel-only: function id instead of a named workload")
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--prec", choices=["fp32_comp", "fp64"], default="fp32_comp")
     ap.add_argument("--csize", type=int, default=32)
     ap.add_argument("--tpr", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--method", choices=["plain", "symmetric"], default="plain")
+    ap.add_argument("--tpp", type=int, default=64, help="kernel-only, symmetric: threads per point")
     args = ap.parse_args()
     if args.warmup < 3 and not args.kernel_only:
         args.warmup = 3

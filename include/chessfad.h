@@ -95,18 +95,33 @@ typedef struct {
     int ld;
 } chessfad_fp_params;
 
+/* Methods. */
+#define CHESSFAD_METHOD_PLAIN 0     /* every chunk of every row: CHUNK-HESS (Alg. 5), CHESS-VEC (Alg. 7) */
+#define CHESSFAD_METHOD_SYMMETRIC 1 /* only chunks from the row's diagonal chunk on: SCHUNK-HESS (Alg. 6),
+                                       SC-HESS-VEC (Alg. 8); about half the evaluations of f (Sec. V) */
+
 /* Launch configuration of the (point, row, chunk) decomposition.
- *   csize            chunk size, 1..32 power of two
- *   threads_per_row  lanes sharing one Hessian row (power of two, 1..32);
- *                    lane r of a row evaluates chunks r, r+tpr, ... and the
- *                    row sum is finished by warp shuffles (Sec. VI, Fig. 2
- *                    does this through shared memory)
- *   block_threads    CTA size, multiple of 32, 32..256
- * Zero in any field means "default". */
+ *   csize             chunk size, 1..32 power of two
+ *   threads_per_row   plain method: lanes sharing one Hessian row (power of
+ *                     two, 1..32); lane r of a row evaluates chunks r, r+tpr,
+ *                     ... and the row sum is finished by warp shuffles
+ *                     (Sec. VI, Fig. 2 does this through shared memory)
+ *   block_threads     plain method: CTA size, multiple of 32, 32..256
+ *   method            CHESSFAD_METHOD_PLAIN or CHESSFAD_METHOD_SYMMETRIC
+ *   threads_per_point symmetric method: threads sharing one point's
+ *                     (row, chunk) items, 32..256 power of two; a CTA holds
+ *                     256 / threads_per_point points (fewer when the staged
+ *                     chunk matrix of an HVP does not fit shared memory)
+ * Zero in any field means "default" (method 0 is the plain method).  The
+ * symmetric HVP stages a point's chunks in shared memory, n (n+1) values per
+ * point: it supports n up to 220 (FP32) / 155 (FP64) and returns
+ * CHESSFAD_ERR_SIZE beyond; the symmetric Hessian has no such limit. */
 typedef struct {
     int csize;
     int threads_per_row;
     int block_threads;
+    int method;
+    int threads_per_point;
 } chessfad_config;
 
 /* out[p][i] = sum_j H(x_p)[i][j] v[p][j] for p < batch (CHESS-VEC, Alg. 7,
@@ -143,10 +158,12 @@ CHESSFAD_API int chessfad_hessian_config(int fn, int n, long long batch, const c
 CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg);
 
 /* Autotune the HVP launch configuration for (fn, n, prec) by timing the
- * candidate (csize, threads_per_row, block_threads) triples on the caller's
- * buffers (x, v, out as for chessfad_hvp; out is overwritten), starting from
- * the Sec. V operation-count model and discarding candidates whose kernels
- * spill registers.  The winner is stored in the process-wide table used by
+ * candidates on the caller's buffers (x, v, out as for chessfad_hvp; out is
+ * overwritten): for every chunk size (largest first, following the Sec. V
+ * operation-count model) the plain method over (threads_per_row,
+ * block_threads) and the symmetric method over threads_per_point, discarding
+ * kernels that spill registers and symmetric HVPs that do not fit shared
+ * memory.  The winner is stored in the process-wide table used by
  * csize = 0 and returned in *best (may be NULL).  Synchronises `stream`.
  * Allocates no device memory. */
 CHESSFAD_API int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,

@@ -42,12 +42,19 @@ class FPParams(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("E", ctypes.c_void_p), ("ld", ctypes.c_int)]
 
 
+PLAIN, SYMMETRIC = 0, 1
+
+
 class Config(ctypes.Structure):
-    """chessfad_config: chunk size, threads per row, CTA size (0 = default)."""
-    _fields_ = [("csize", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("block_threads", ctypes.c_int)]
+    """chessfad_config: chunk size, threads per row, CTA size (plain method),
+    method, threads per point (symmetric method); 0 = default."""
+    _fields_ = [("csize", ctypes.c_int), ("threads_per_row", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("method", ctypes.c_int), ("threads_per_point", ctypes.c_int)]
 
     def as_dict(self) -> dict:
-        return {"csize": self.csize, "threads_per_row": self.threads_per_row, "block_threads": self.block_threads}
+        return {"csize": self.csize, "threads_per_row": self.threads_per_row, "block_threads": self.block_threads,
+                "method": "symmetric" if self.method == SYMMETRIC else "plain",
+                "threads_per_point": self.threads_per_point}
 
 
 def library_path() -> str:

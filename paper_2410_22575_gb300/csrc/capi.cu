@@ -36,19 +36,32 @@ static std::map<std::tuple<int, int, int>, chessfad_config> g_table;
 // Default: the largest chunk that keeps the hDual state comfortably in
 // registers (the plain method's multiplication count (6 + 3/c) n^2 M falls
 // with c, Sec. V), one chunk per lane where a row has <= 32 chunks.
-static chessfad_config default_config(int fn, int n, int prec)
+// Rows (point, i) that fill the GPU several times over with one thread each.
+static constexpr long long kRowsOneLane = 4LL * 152 * 256;
+
+static int default_threads_per_point(int n, long long batch);
+
+static chessfad_config default_config(int fn, int n, long long batch, int prec)
 {
     chessfad_config c{};
     int cmax = (prec == CHESSFAD_FP64) ? 8 : 16;
-    if (fn == CHESSFAD_FLETCHER_POWELL) cmax = (prec == CHESSFAD_FP64) ? 4 : 8;
+    if (fn == CHESSFAD_FLETCHER_POWELL) cmax = (prec == CHESSFAD_FP64) ? 4 : 16;
     c.csize = std::min(cmax, next_pow2(n));
     const int nch = (n + c.csize - 1) / c.csize;
-    c.threads_per_row = std::min(32, next_pow2(nch));
+    // Enough rows: one thread per row sweeps all of the row's chunks (the
+    // per-point prologue is amortised over the most work).  Few rows: spread
+    // a row's chunks over lanes (the paper's L2) to fill the GPU.
+    int tpr = 1;
+    const long long rows = batch * (long long)n;
+    while (tpr < 32 && tpr < nch && rows * tpr < kRowsOneLane) tpr <<= 1;
+    c.threads_per_row = tpr;
     c.block_threads = 256;
+    c.method = CHESSFAD_METHOD_PLAIN;
+    c.threads_per_point = default_threads_per_point(n, batch);
     return c;
 }
 
-static chessfad_config resolve(int fn, int n, int prec, const chessfad_config *cfg, int csize_hint)
+static chessfad_config resolve(int fn, int n, long long batch, int prec, const chessfad_config *cfg, int csize_hint)
 {
     chessfad_config c{};
     if (cfg) c = *cfg;
@@ -56,14 +69,20 @@ static chessfad_config resolve(int fn, int n, int prec, const chessfad_config *c
     if (c.csize == 0) {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_table.find(std::make_tuple(fn, n, prec));
-        chessfad_config base = (it != g_table.end()) ? it->second : default_config(fn, n, prec);
+        chessfad_config base = (it != g_table.end()) ? it->second : default_config(fn, n, batch, prec);
         if (c.threads_per_row == 0) c.threads_per_row = base.threads_per_row;
         if (c.block_threads == 0) c.block_threads = base.block_threads;
+        if (c.threads_per_point == 0) c.threads_per_point = base.threads_per_point;
+        if (!cfg || cfg->method == 0) c.method = base.method;
         c.csize = base.csize;
     }
-    const int nch = (n + c.csize - 1) / c.csize;
-    if (c.threads_per_row == 0) c.threads_per_row = std::min(32, next_pow2(nch));
-    if (c.block_threads == 0) c.block_threads = 256;
+    if (c.threads_per_point == 0) c.threads_per_point = default_threads_per_point(n, batch);
+    if (c.threads_per_row == 0 || c.block_threads == 0) {
+        chessfad_config d = default_config(fn, n, batch, prec);
+        const int nch = (n + c.csize - 1) / c.csize;
+        if (c.threads_per_row == 0) c.threads_per_row = std::min(d.threads_per_row, std::max(1, next_pow2(nch)));
+        if (c.block_threads == 0) c.block_threads = d.block_threads;
+    }
     return c;
 }
 
@@ -85,7 +104,19 @@ static int check_config(const chessfad_config &c)
     const int t = c.threads_per_row;
     if (t < 1 || t > 32 || (t & (t - 1))) return CHESSFAD_ERR_CONFIG;
     if (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32) return CHESSFAD_ERR_CONFIG;
+    if (c.method != CHESSFAD_METHOD_PLAIN && c.method != CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_CONFIG;
+    const int p = c.threads_per_point;
+    if (p < 32 || p > 256 || (p & (p - 1))) return CHESSFAD_ERR_CONFIG;
     return CHESSFAD_SUCCESS;
+}
+
+// Symmetric method: threads per point that fill the GPU several times over.
+static int default_threads_per_point(int n, long long batch)
+{
+    (void)n;
+    int p = 32;
+    while (p < 256 && batch * (long long)p < kRowsOneLane) p <<= 1;
+    return p;
 }
 
 // Rows of A and B staged per shared-memory tile by the Fletcher-Powell sweep:
@@ -122,6 +153,36 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
     if (fn == CHESSFAD_FLETCHER_POWELL && a.mt % fp_mb(c.csize) != 0) return CHESSFAD_ERR_CONFIG;
     cudaError_t e = cudaErrorInvalidValue;
     const bool f64 = (prec == CHESSFAD_FP64);
+    if (c.method == CHESSFAD_METHOD_SYMMETRIC && !(!f64 && n == 1)) {
+        // Symmetric method: a.maxpts = points per block, a.tpp = threads per
+        // point; as many points per CTA as shared memory allows (<= 200 KiB).
+        a.tpp = c.threads_per_point;
+        auto bytes = [&](int ppb) {
+            a.maxpts = ppb;
+            switch (fn) {
+            case CHESSFAD_ROSENBROCK: return f64 ? smem_rosenbrock_f64_sym(c.csize, hvp, a) : smem_rosenbrock_f32c_sym(c.csize, hvp, a);
+            case CHESSFAD_ACKLEY: return f64 ? smem_ackley_f64_sym(c.csize, hvp, a) : smem_ackley_f32c_sym(c.csize, hvp, a);
+            default: return f64 ? smem_fp_f64_sym(c.csize, hvp, a) : smem_fp_f32c_sym(c.csize, hvp, a);
+            }
+        };
+        int ppb = (int)std::min<long long>(batch, 256 / c.threads_per_point);
+        const size_t kBudget = 200 * 1024;
+        while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
+        if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
+        a.maxpts = ppb;
+        switch (fn) {
+        case CHESSFAD_ROSENBROCK:
+            e = f64 ? launch_rosenbrock_f64_sym(c.csize, hvp, a, stream) : launch_rosenbrock_f32c_sym(c.csize, hvp, a, stream);
+            break;
+        case CHESSFAD_ACKLEY:
+            e = f64 ? launch_ackley_f64_sym(c.csize, hvp, a, stream) : launch_ackley_f32c_sym(c.csize, hvp, a, stream);
+            break;
+        case CHESSFAD_FLETCHER_POWELL:
+            e = f64 ? launch_fp_f64_sym(c.csize, hvp, a, stream) : launch_fp_f32c_sym(c.csize, hvp, a, stream);
+            break;
+        }
+        return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+    }
     if (!f64 && n == 1) {
         // One variable: compute in FP64 (float I/O), see dispatch.h.
         a.nch = 1;
@@ -168,7 +229,7 @@ static int run(int fn, int n, long long batch, const chessfad_config *cfg, int c
     if (st) return st;
     if (csize_hint != 0 && !valid_chunk(csize_hint)) return CHESSFAD_ERR_CHUNK;
     if (cfg && cfg->csize != 0 && !valid_chunk(cfg->csize)) return CHESSFAD_ERR_CHUNK;
-    const chessfad_config c = resolve(fn, n, prec, cfg, csize_hint);
+    const chessfad_config c = resolve(fn, n, batch, prec, cfg, csize_hint);
     st = check_config(c);
     if (st) return st;
     if (batch == 0) return CHESSFAD_SUCCESS;
@@ -213,7 +274,7 @@ int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_c
     if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
     if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
     if (batch < 0) return CHESSFAD_ERR_BATCH;
-    *cfg = resolve(fn, n, prec, nullptr, 0);
+    *cfg = resolve(fn, n, batch, prec, nullptr, 0);
     return CHESSFAD_SUCCESS;
 }
 
@@ -246,36 +307,38 @@ int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const v
     chessfad_config win{};
     float win_ms = INFINITY;
     int rc = CHESSFAD_SUCCESS;
+    // Candidates: plain method over (threads/row, CTA size), symmetric method
+    // (Alg. 8) over threads/point; kernels that spill are skipped.
+    std::vector<chessfad_config> cands;
     for (int c : chunks) {
         cudaFuncAttributes fa{};
         if (kernel_attr(fn, prec, c, true, &fa) != cudaSuccess || fa.localSizeBytes > kMaxFrameNoSpill) continue;
         const int nch = (n + c - 1) / c;
         const int tmax = std::min(32, next_pow2(nch));
-        for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1) {
-            for (int bt : {256, 128}) {
-                chessfad_config cfg{c, t, bt};
-                if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {
-                    cudaGetLastError();
-                    continue;
-                }
-                cudaEventRecord(e0, stream);
-                const int reps = 3;
-                for (int k = 0; k < reps; ++k) launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream);
-                cudaEventRecord(e1, stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    rc = CHESSFAD_ERR_CUDA;
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < win_ms) {
-                    win_ms = ms;
-                    win = cfg;
-                }
-            }
-            if (rc) break;
+        for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
+            for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
+        if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
+        for (int p : {32, 64, 128}) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_SYMMETRIC, p});
+    }
+    for (const chessfad_config &cfg : cands) {
+        if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {
+            cudaGetLastError();
+            continue;  // e.g. a symmetric HVP whose staged chunks exceed shared memory
         }
-        if (rc) break;
+        cudaEventRecord(e0, stream);
+        const int reps = 3;
+        for (int k = 0; k < reps; ++k) launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = CHESSFAD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < win_ms) {
+            win_ms = ms;
+            win = cfg;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -29,6 +29,18 @@ cudaError_t launch_rosenbrock_f64io32(bool hvp, const SweepArgs &a, int block_th
 cudaError_t launch_ackley_f64io32(bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream);
 cudaError_t launch_fp_f64io32(bool hvp, const SweepArgs &a, int block_threads, cudaStream_t stream);
 
+// Symmetric variants (SCHUNK-HESS, SC-HESS-VEC): a.maxpts = points per block,
+// a.tpp = threads per point.
+#define CHESSFAD_SYM(name) cudaError_t launch_##name##_sym(int C, bool hvp, const SweepArgs &a, cudaStream_t stream); \
+    size_t smem_##name##_sym(int C, bool hvp, const SweepArgs &a)
+CHESSFAD_SYM(rosenbrock_f64);
+CHESSFAD_SYM(rosenbrock_f32c);
+CHESSFAD_SYM(ackley_f64);
+CHESSFAD_SYM(ackley_f32c);
+CHESSFAD_SYM(fp_f64);
+CHESSFAD_SYM(fp_f32c);
+#undef CHESSFAD_SYM
+
 // cudaFuncGetAttributes of the instantiation (registers, local memory).
 #define CHESSFAD_ATTR(name) cudaError_t name(int C, bool hvp, cudaFuncAttributes *fa)
 CHESSFAD_ATTR(attr_rosenbrock_f64);

@@ -44,4 +44,45 @@ cudaError_t attr_ackley_f32c(int C, bool hvp, cudaFuncAttributes *fa)
     return cudaErrorInvalidValue;
 }
 
+// Symmetric variants (SCHUNK-HESS / SC-HESS-VEC): launch and shared-memory size.
+template <int C>
+static cudaError_t go_sym(bool hvp, const SweepArgs &a, cudaStream_t s)
+{
+    constexpr int MB = fp_mb(C);
+    return hvp ? launch_sym<float, float, C, FN_ACKLEY, true, MB>(a, s) : launch_sym<float, float, C, FN_ACKLEY, false, MB>(a, s);
+}
+
+template <int C>
+static size_t bytes_sym(bool hvp, const SweepArgs &a)
+{
+    constexpr int MB = fp_mb(C);
+    return hvp ? sym_smem_bytes<float, float, C, FN_ACKLEY, true, MB>(a) : sym_smem_bytes<float, float, C, FN_ACKLEY, false, MB>(a);
+}
+
+cudaError_t launch_ackley_f32c_sym(int C, bool hvp, const SweepArgs &a, cudaStream_t s)
+{
+    switch (C) {
+    case 1: return go_sym<1>(hvp, a, s);
+    case 2: return go_sym<2>(hvp, a, s);
+    case 4: return go_sym<4>(hvp, a, s);
+    case 8: return go_sym<8>(hvp, a, s);
+    case 16: return go_sym<16>(hvp, a, s);
+    case 32: return go_sym<32>(hvp, a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+size_t smem_ackley_f32c_sym(int C, bool hvp, const SweepArgs &a)
+{
+    switch (C) {
+    case 1: return bytes_sym<1>(hvp, a);
+    case 2: return bytes_sym<2>(hvp, a);
+    case 4: return bytes_sym<4>(hvp, a);
+    case 8: return bytes_sym<8>(hvp, a);
+    case 16: return bytes_sym<16>(hvp, a);
+    case 32: return bytes_sym<32>(hvp, a);
+    }
+    return 0;
+}
+
 }  // namespace chessfad

@@ -140,11 +140,14 @@ struct IsComp<float> {
 
 // ------------------------------------------------------------------ seeding
 // The seeded variables y_0 .. y_{n-1} of one sweep (CHUNK-INIT, Alg. 4) are
-// visited in ascending order in three segments: before the chunk, the chunk,
-// after the chunk.  Outside the chunk the g part is the constant zero vector;
-// inside, when the chunk is unrolled, the constant unit vector e_{k-cstart}.
-// Only the d/dx_i seed [k == i] is data dependent.  Chunks wider than the
-// unroll limit walk their variables with the generic (select-based) seed.
+// visited as: every variable outside the chunk (ascending), then the chunk's.
+// Outside the chunk the g part is the constant zero vector; inside, when the
+// chunk is unrolled, the constant unit vector e_{k-cstart}; only the d/dx_i
+// seed [k == i] is data dependent.  The loop over the variables outside the
+// chunk has the same trip count (n - C) for every chunk except a ragged last
+// one, so lanes of a warp that work on different chunks do not diverge.
+// Chunks wider than the unroll limit walk their variables with the generic
+// (select-based) seed.
 template <int C, int LIMIT>
 struct Unroll {
     static constexpr bool value = C <= LIMIT;
@@ -162,54 +165,81 @@ struct StaticFor {
     }
 };
 
-// f(k, y_k) for k = 0 .. n-1.
-template <typename T, int C, int LIMIT, typename F>
+// f(k, y_k) for every k in 0 .. n-1.  kRemap: the variables outside the chunk
+// in one loop of uniform trip count, then the chunk (lanes of a warp on
+// different chunks stay converged); otherwise three segments in ascending
+// order (cheapest when a warp's lanes share the chunk).
+template <typename T, int C, int LIMIT, bool kRemap, typename F>
 __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
     const int lo = min(cstart, n), hi = min(cstart + C, n);
-    for (int k = 0; k < lo; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
-    if constexpr (Unroll<C, LIMIT>::value) {
-        StaticFor<0, C>::run([&](auto P) {
-            const int k = cstart + P.value;
-            if (k < n) f(k, seed_at<T, C, P.value>(xs[k], k == i));
-        });
+    auto chunk = [&]() {
+        if constexpr (Unroll<C, LIMIT>::value) {
+            StaticFor<0, C>::run([&](auto P) {
+                const int k = cstart + P.value;
+                if (k < n) f(k, seed_at<T, C, P.value>(xs[k], k == i));
+            });
+        } else {
+            for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart));
+        }
+    };
+    if constexpr (kRemap) {
+        const int nout = n - (hi - lo);
+        for (int kk = 0; kk < nout; ++kk) {
+            const int k = kk < lo ? kk : kk + (hi - lo);
+            f(k, seed_at<T, C, -1>(xs[k], k == i));
+        }
+        chunk();
     } else {
-        for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart));
+        for (int k = 0; k < lo; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
+        chunk();
+        for (int k = hi; k < n; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
     }
-    for (int k = hi; k < n; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
 }
 
-// f(y_k, y_{k+1}) for k = 0 .. n-2 (functions whose terms couple neighbours).
-template <typename T, int C, int LIMIT, typename F>
+// f(y_k, y_{k+1}) for every k in 0 .. n-2 (functions whose terms couple
+// neighbours).  The pairs touching the chunk are k - cstart in [-1, C-1];
+// kRemap as for for_each_seed.
+template <typename T, int C, int LIMIT, bool kRemap, typename F>
 __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
-    const int a_end = min(cstart - 1, n - 1);
-    for (int k = 0; k < a_end; ++k) f(seed_at<T, C, -1>(xs[k], k == i), seed_at<T, C, -1>(xs[k + 1], k + 1 == i));
-    if constexpr (Unroll<C, LIMIT>::value) {
-        // pairs touching the chunk: k - cstart = t in [-1, C-1]
-        StaticFor<0, C + 1>::run([&](auto Q) {
-            constexpr int t = decltype(Q)::value - 1;
-            const int k = cstart + t;
-            if (k >= 0 && k + 1 < n)
-                f(seed_at<T, C, t>(xs[k], k == i), seed_at<T, C, t + 1>(xs[k + 1], k + 1 == i));
-        });
-    } else {
-        const int b_end = min(cstart + C, n - 1);
-        for (int k = max(cstart - 1, 0); k < b_end; ++k)
-            f(seed<T, C>(xs[k], k, i, cstart), seed<T, C>(xs[k + 1], k + 1, i, cstart));
-    }
-    for (int k = cstart + C; k < n - 1; ++k)
+    const int t0 = max(cstart - 1, 0);
+    const int t1 = max(t0, min(cstart + C, n - 1));
+    auto outside = [&](int k) {
         f(seed_at<T, C, -1>(xs[k], k == i), seed_at<T, C, -1>(xs[k + 1], k + 1 == i));
+    };
+    auto touching = [&]() {
+        if constexpr (Unroll<C, LIMIT>::value) {
+            StaticFor<0, C + 1>::run([&](auto Q) {
+                constexpr int t = decltype(Q)::value - 1;
+                const int k = cstart + t;
+                if (k >= 0 && k + 1 < n)
+                    f(seed_at<T, C, t>(xs[k], k == i), seed_at<T, C, t + 1>(xs[k + 1], k + 1 == i));
+            });
+        } else {
+            for (int k = t0; k < t1; ++k)
+                f(seed<T, C>(xs[k], k, i, cstart), seed<T, C>(xs[k + 1], k + 1, i, cstart));
+        }
+    };
+    if constexpr (kRemap) {
+        const int nout = max(0, n - 1 - (t1 - t0));
+        for (int kk = 0; kk < nout; ++kk) outside(kk < t0 ? kk : kk + (t1 - t0));
+        touching();
+    } else {
+        for (int k = 0; k < t0; ++k) outside(k);
+        touching();
+        for (int k = t1; k < n - 1; ++k) outside(k);
+    }
 }
 
 // ------------------------------------------------------------------ functions
 // Rosenbrock, f = sum_{k<n-1} 100 (x_{k+1} - x_k^2)^2 + (1 - x_k)^2, on hDuals.
-template <typename T, int C>
+template <typename T, int C, bool kRemap>
 __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, int n, int i, int cstart)
 {
     TermSum<T, C, IsComp<T>::value> acc;
     acc.init();
-    for_each_pair<T, C, 8>(xs, n, i, cstart, [&](const HD<T, C> &y0, const HD<T, C> &y1) {
+    for_each_pair<T, C, 8, kRemap>(xs, n, i, cstart, [&](const HD<T, C> &y0, const HD<T, C> &y1) {
         const HD<T, C> d = hsub(y1, hmul(y0, y0));  // x_{k+1} - x_k^2
         const HD<T, C> w = smul(T(100), d);           // 100 (x_{k+1} - x_k^2)
         const HD<T, C> e = rsub(T(1), y0);            // 1 - x_k
@@ -224,14 +254,14 @@ __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, i
 // Cs receives at most one nonzero term under CHUNK-INIT seeding (y_k carries
 // a nonzero d/dx only for k == i or k in the chunk), so these sums are exact
 // up to that term's own rounding and need no compensation.
-template <typename T, int C>
+template <typename T, int C, bool kRemap>
 __device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const T *__restrict__ dcos1,
                                                  const T *__restrict__ dcos2, const T *__restrict__ sc, int n,
                                                  int i, int cstart)
 {
     HD<T, C> S = hzero<T, C>();
     HD<T, C> Cs = hzero<T, C>();
-    for_each_seed<T, C, 16>(xs, n, i, cstart, [&](int k, const HD<T, C> &y) {
+    for_each_seed<T, C, 16, kRemap>(xs, n, i, cstart, [&](int k, const HD<T, C> &y) {
         S = hfma(y, y, S);
         // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
         add_unary<false>(Cs, y, T(0), dcos1[k], dcos2[k]);
@@ -283,27 +313,17 @@ struct ListPoints {
     __device__ __forceinline__ const double *e(long long p) const { return Epack + eoffs[list[p]]; }
 };
 
-// T is the arithmetic type of the sweep, IO the element type of x, v and the
-// output (IO = T except for the one-variable compensated-FP32 case, which
-// computes in FP64 with float I/O).  Every thread of the block must call it
-// (it synchronises the block).
-template <typename T, typename IO, int C, int FN, bool HVP, int MB, typename PM>
-__device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigned char *smem_raw)
+// Stage the x (and v) of the points p0 .. p0+npts-1 into shared memory and
+// build their per-point value tables (the FP64 islands).  Every thread of the
+// block calls it; it ends with the block synchronised.
+template <typename T, typename IO, int FN, bool HVP, typename PM>
+__device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsigned char *smem_raw, const Smem<T> &L,
+                                               long long p0, int npts)
 {
     const int n = a.n;
-    const Smem<T> L = smem_layout<T>(FN, HVP, n, a.maxpts, a.mt);
+    const int tid = threadIdx.x;
     T *xs = reinterpret_cast<T *>(smem_raw + L.xs);
     T *vs = reinterpret_cast<T *>(smem_raw + L.vs);
-
-    const int rows_per_block = blockDim.x / a.tpr;
-    const long long p0 = a.row0 / n;
-    long long plast = (a.row0 + rows_per_block - 1) / n;
-    if (plast > a.npoints - 1) plast = a.npoints - 1;
-    const int npts = (int)(plast - p0 + 1);
-    const int tid = threadIdx.x;
-
-    // ---- stage x (and v) of this block's points (n contiguous values each;
-    // one contiguous range for a contiguous batch).
     {
         const IO *X = reinterpret_cast<const IO *>(a.x);
         const IO *V = reinterpret_cast<const IO *>(a.v);
@@ -317,7 +337,6 @@ __device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigne
     }
     __syncthreads();
 
-    // ---- per-point value tables (FP64 islands)
     if (FN == FN_ACKLEY) {
         T *t1 = reinterpret_cast<T *>(smem_raw + L.t1);
         T *t2 = reinterpret_cast<T *>(smem_raw + L.t2);
@@ -355,18 +374,35 @@ __device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigne
                 Cv += __shfl_xor_sync(0xffffffffu, Cv, off);
             }
             if (lane == 0) {
-                const double nn = (double)n;
-                const double a0 = S / nn;
-                const double sq = sqrt(a0);
                 T *o = sc + q * kAckScal;
-                o[0] = (T)S;
-                o[1] = (T)Cv;
-                o[2] = (T)(1.0 / nn);
-                o[3] = (T)sq;                        // sqrt at S/n
-                o[4] = (T)(0.5 / sq);                // its first derivative
-                o[5] = (T)(-0.25 / (sq * a0));       // its second derivative
-                o[6] = (T)exp(-0.2 * sq);            // exp at -0.2 sqrt(S/n)
-                o[7] = (T)exp(Cv / nn);              // exp at C/n
+                if (sizeof(T) == 8) {
+                    const double nn = (double)n;
+                    const double a0 = S / nn;
+                    const double sq = sqrt(a0);
+                    o[0] = (T)S;
+                    o[1] = (T)Cv;
+                    o[2] = (T)(1.0 / nn);
+                    o[3] = (T)sq;                        // sqrt at S/n
+                    o[4] = (T)(0.5 / sq);                // its first derivative
+                    o[5] = (T)(-0.25 / (sq * a0));       // its second derivative
+                    o[6] = (T)exp(-0.2 * sq);            // exp at -0.2 sqrt(S/n)
+                    o[7] = (T)exp(Cv / nn);              // exp at C/n
+                } else {
+                    // The sums are FP64 (the island); the scalar functions of
+                    // them only feed FP32 arithmetic, so they are evaluated in
+                    // FP32 from the correctly rounded arguments, off the slow
+                    // FP64 pipe.
+                    const float a0 = (float)(S / (double)n);
+                    const float sq = sqrtf(a0);
+                    o[0] = (T)S;
+                    o[1] = (T)Cv;
+                    o[2] = (T)(1.0f / (float)n);
+                    o[3] = (T)sq;
+                    o[4] = (T)(0.5f / sq);
+                    o[5] = (T)(-0.25f / (sq * a0));
+                    o[6] = (T)expf(-0.2f * sq);
+                    o[7] = (T)expf((float)(Cv / (double)n));
+                }
             }
         }
         __syncthreads();
@@ -400,6 +436,128 @@ __device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigne
         }
         __syncthreads();
     }
+}
+
+// Fletcher-Powell on hDuals for one (row i, chunk at cstart):
+// f = sum_m r_m^2, r_m = E_m - sum_j (A_mj sin y_j + B_mj cos y_j).  A and B
+// stream through shared memory in tiles of mt rows, stored transposed
+// ([j][m]) so a thread reads MB consecutive rows per j; MB residual hDuals are
+// accumulated in registers at once so each seeded y_j serves MB rows.  The
+// tile loads are block-wide: every thread of the block makes the same calls
+// (threads without a sweep pass has = false); with a single tile the load
+// happens only when `reload` is set.
+template <typename T, int C, int MB, bool kRemap>
+__device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_raw, const Smem<T> &L, const T *xq,
+                                             const T *ts, const T *tc, const T *res, int i, int cstart, bool has,
+                                             bool reload)
+{
+    const int n = a.n;
+    const int tid = threadIdx.x;
+    T *At = reinterpret_cast<T *>(smem_raw + L.at);
+    T *Bt = reinterpret_cast<T *>(smem_raw + L.bt);
+    const int mt = a.mt;
+    const int ntiles = (n + mt - 1) / mt;
+    TermSum<T, C, IsComp<T>::value> acc;
+    acc.init();
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int m0 = tile * mt;
+        if (ntiles > 1 || reload) {
+            __syncthreads();
+            const int cnt = mt * n;
+            for (int e = tid; e < cnt; e += blockDim.x) {
+                const int mm = e / n, jj = e - mm * n;
+                const int m = m0 + mm;
+                T av = T(0), bv = T(0);
+                if (m < n) {
+                    av = (T)a.A[(size_t)m * a.ld + jj];
+                    bv = (T)a.B[(size_t)m * a.ld + jj];
+                }
+                At[jj * mt + mm] = av;
+                Bt[jj * mt + mm] = bv;
+            }
+            __syncthreads();
+        }
+        if (!has) continue;
+        const int mend = min(m0 + mt, n);
+        for (int mb = m0; mb < mend; mb += MB) {
+            HD<T, C> s[MB];
+#pragma unroll
+            for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
+            for_each_seed<T, C, 16, kRemap>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
+                const T sj = ts[jv], cj = tc[jv];
+                const T *ar = At + jv * mt + (mb - m0);
+                const T *br = Bt + jv * mt + (mb - m0);
+#pragma unroll
+                for (int u = 0; u < MB; ++u) {
+                    sfma_unary<false>(s[u], ar[u], y, sj, cj, -sj);   // + A_mj sin y_j
+                    sfma_unary<false>(s[u], br[u], y, cj, -sj, -cj);  // + B_mj cos y_j
+                }
+            });
+#pragma unroll
+            for (int u = 0; u < MB; ++u) {
+                if (mb + u < mend) {
+                    HD<T, C> rr = rsub(T(0), s[u]);
+                    rr.v = res[mb + u];  // E_m - sum_j (...)  (FP64 island)
+                    acc.add_prod(rr, rr);
+                }
+            }
+        }
+    }
+    return acc.value();
+}
+
+// Per-point table pointers of staged point q.
+template <typename T>
+struct PointTables {
+    const T *x, *v, *t1, *t2, *sc, *res;
+    __device__ __forceinline__ PointTables(unsigned char *smem_raw, const Smem<T> &L, int q, int n)
+    {
+        x = reinterpret_cast<const T *>(smem_raw + L.xs) + q * n;
+        v = reinterpret_cast<const T *>(smem_raw + L.vs) + q * n;
+        t1 = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
+        t2 = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
+        sc = reinterpret_cast<const T *>(smem_raw + L.sc) + q * kAckScal;
+        res = reinterpret_cast<const T *>(smem_raw + L.res) + q * n;
+    }
+};
+
+// f's hDual for (row i, chunk at cstart) of a staged point.  Rosenbrock and
+// Ackley sweeps are per-thread; Fletcher-Powell's is block-uniform (see
+// fp_sweep), so every thread calls this with the same trip counts.
+template <typename T, int C, int FN, int MB, bool kRemap>
+__device__ __forceinline__ HD<T, C> row_chunk(const Job &a, unsigned char *smem_raw, const Smem<T> &L,
+                                              const PointTables<T> &pt, int i, int cstart, bool has, bool reload)
+{
+    if constexpr (FN == FN_ROSENBROCK) {
+        if (has) return rosenbrock_sweep<T, C, kRemap>(pt.x, a.n, i, cstart);
+        return hzero<T, C>();
+    } else if constexpr (FN == FN_ACKLEY) {
+        if (has) return ackley_sweep<T, C, kRemap>(pt.x, pt.t1, pt.t2, pt.sc, a.n, i, cstart);
+        return hzero<T, C>();
+    } else {
+        return fp_sweep<T, C, MB, kRemap>(a, smem_raw, L, pt.x, pt.t1, pt.t2, pt.res, i, cstart, has, reload);
+    }
+}
+
+// T is the arithmetic type of the sweep, IO the element type of x, v and the
+// output (IO = T except for the one-variable compensated-FP32 case, which
+// computes in FP64 with float I/O).  Every thread of the block must call it
+// (it synchronises the block).  CHESS-VEC / CHUNK-HESS (Alg. 7 / Alg. 5):
+// every chunk of every row is evaluated.
+template <typename T, typename IO, int C, int FN, bool HVP, int MB, typename PM>
+__device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigned char *smem_raw)
+{
+    const int n = a.n;
+    const Smem<T> L = smem_layout<T>(FN, HVP, n, a.maxpts, a.mt);
+
+    const int rows_per_block = blockDim.x / a.tpr;
+    const long long p0 = a.row0 / n;
+    long long plast = (a.row0 + rows_per_block - 1) / n;
+    if (plast > a.npoints - 1) plast = a.npoints - 1;
+    const int npts = (int)(plast - p0 + 1);
+    const int tid = threadIdx.x;
+
+    point_prologue<T, IO, FN, HVP>(a, pm, smem_raw, L, p0, npts);
 
     // ---- this thread's (point, row, lane)
     const long long row = a.row0 + tid / a.tpr;
@@ -408,8 +566,7 @@ __device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigne
     const int i = (int)(row - p * n);
     const bool active = p < a.npoints;
     const int q = active ? (int)(p - p0) : 0;
-    const T *xq = xs + q * n;
-    const T *vq = vs + q * n;
+    const PointTables<T> pt(smem_raw, L, q, n);
 
     using Dot = typename std::conditional<IsComp<T>::value, CSum, T>::type;
     Dot dot;
@@ -420,104 +577,33 @@ __device__ __forceinline__ void block_sweeps(const Job &a, const PM &pm, unsigne
         dot = T(0);
     }
 
-    auto emit = [&](const HD<T, C> &f, int cstart) {
+    // Uniform trip count for the block-wide Fletcher-Powell tiles; the other
+    // functions simply skip the iterations a lane has no chunk for.
+    const int iters = (a.nch + a.tpr - 1) / a.tpr;
+    for (int it = 0; it < iters; ++it) {
+        const int j = r + it * a.tpr;
+        const bool has = j < a.nch;
+        if (FN != FN_FP && !has) break;
+        const int cstart = j * C;
+        // One lane per row: a warp's lanes share the chunk, the three-segment
+        // loop is cheapest.  Several lanes per row: lanes differ in chunk,
+        // the uniform-trip-count loop keeps them converged.
+        const HD<T, C> f = (a.tpr == 1) ? row_chunk<T, C, FN, MB, false>(a, smem_raw, L, pt, i, cstart, has, it == 0)
+                                        : row_chunk<T, C, FN, MB, true>(a, smem_raw, L, pt, i, cstart, has, it == 0);
+        if (!has) continue;
         if constexpr (HVP) {
 #pragma unroll
             for (int l = 0; l < C; ++l) {
                 if (cstart + l < n) {
-                    if constexpr (IsComp<T>::value) cdot_add(dot, f.h[l], vq[cstart + l]);
-                    else dot = fma_(f.h[l], vq[cstart + l], dot);
+                    if constexpr (IsComp<T>::value) cdot_add(dot, f.h[l], pt.v[cstart + l]);
+                    else dot = fma_(f.h[l], pt.v[cstart + l], dot);
                 }
             }
-        } else {
-            if (active) {
-                IO *H = reinterpret_cast<IO *>(a.out) + (pm.off(p) + i) * n;
+        } else if (active) {
+            IO *H = reinterpret_cast<IO *>(a.out) + (pm.off(p) + i) * n;
 #pragma unroll
-                for (int l = 0; l < C; ++l)
-                    if (cstart + l < n) H[cstart + l] = (IO)f.h[l];
-            }
-        }
-    };
-
-    if constexpr (FN == FN_ROSENBROCK) {
-        for (int j = r; j < a.nch; j += a.tpr) {
-            const int cstart = j * C;
-            emit(rosenbrock_sweep<T, C>(xq, n, i, cstart), cstart);
-        }
-    } else if constexpr (FN == FN_ACKLEY) {
-        const T *t1 = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
-        const T *t2 = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
-        const T *sc = reinterpret_cast<const T *>(smem_raw + L.sc) + q * kAckScal;
-        for (int j = r; j < a.nch; j += a.tpr) {
-            const int cstart = j * C;
-            emit(ackley_sweep<T, C>(xq, t1, t2, sc, n, i, cstart), cstart);
-        }
-    } else {
-        // Fletcher-Powell: f = sum_m r_m^2, r_m = E_m - sum_j (A_mj sin y_j +
-        // B_mj cos y_j).  A and B stream through shared memory in tiles of mt
-        // rows, stored transposed ([j][m]) so a thread reads MB consecutive
-        // rows per j; MB residual hDuals are accumulated in registers at once
-        // so each seeded y_j is reused MB times.  All threads of the block walk
-        // the tiles together (uniform trip counts around __syncthreads).
-        const T *ts = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
-        const T *tc = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
-        const T *res = reinterpret_cast<const T *>(smem_raw + L.res) + q * n;
-        T *At = reinterpret_cast<T *>(smem_raw + L.at);
-        T *Bt = reinterpret_cast<T *>(smem_raw + L.bt);
-        const int mt = a.mt;
-        const int ntiles = (n + mt - 1) / mt;
-        const int iters = (a.nch + a.tpr - 1) / a.tpr;
-        for (int it = 0; it < iters; ++it) {
-            const int j = r + it * a.tpr;
-            const bool has = j < a.nch;
-            const int cstart = j * C;
-            TermSum<T, C, IsComp<T>::value> acc;
-            acc.init();
-            for (int tile = 0; tile < ntiles; ++tile) {
-                const int m0 = tile * mt;
-                if (ntiles > 1 || it == 0) {
-                    __syncthreads();
-                    const int cnt = mt * n;
-                    for (int e = tid; e < cnt; e += blockDim.x) {
-                        const int mm = e / n, jj = e - mm * n;
-                        const int m = m0 + mm;
-                        T av = T(0), bv = T(0);
-                        if (m < n) {
-                            av = (T)a.A[(size_t)m * a.ld + jj];
-                            bv = (T)a.B[(size_t)m * a.ld + jj];
-                        }
-                        At[jj * mt + mm] = av;
-                        Bt[jj * mt + mm] = bv;
-                    }
-                    __syncthreads();
-                }
-                if (!has) continue;
-                const int mend = min(m0 + mt, n);
-                for (int mb = m0; mb < mend; mb += MB) {
-                    HD<T, C> s[MB];
-#pragma unroll
-                    for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
-                    for_each_seed<T, C, 16>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
-                        const T sj = ts[jv], cj = tc[jv];
-                        const T *ar = At + jv * mt + (mb - m0);
-                        const T *br = Bt + jv * mt + (mb - m0);
-#pragma unroll
-                        for (int u = 0; u < MB; ++u) {
-                            sfma_unary<false>(s[u], ar[u], y, sj, cj, -sj);   // + A_mj sin y_j
-                            sfma_unary<false>(s[u], br[u], y, cj, -sj, -cj);  // + B_mj cos y_j
-                        }
-                    });
-#pragma unroll
-                    for (int u = 0; u < MB; ++u) {
-                        if (mb + u < mend) {
-                            HD<T, C> rr = rsub(T(0), s[u]);
-                            rr.v = res[mb + u];  // E_m - sum_j (...)  (FP64 island)
-                            acc.add_prod(rr, rr);
-                        }
-                    }
-                }
-            }
-            if (has) emit(acc.value(), cstart);
+            for (int l = 0; l < C; ++l)
+                if (cstart + l < n) H[cstart + l] = (IO)f.h[l];
         }
     }
 
@@ -564,27 +650,180 @@ __global__ void __launch_bounds__(256, 1) sweep_kernel(const SweepArgs a)
     block_sweeps<T, IO, C, FN, HVP, MB>(job, pm, smem_raw);
 }
 
-// Host-side launch helper: computes the layout, opts into large dynamic
-// shared memory once per (kernel, device), launches, and reports the error.
+// ------------------------------------------------------------------ symmetric
+// SCHUNK-HESS (Alg. 6) and SC-HESS-VEC (Alg. 8): a row evaluates only the
+// chunks from its diagonal chunk on.  The items of one point are the pairs
+// (row i, chunk cn) with cn >= floor(i/C), enumerated by chunk-block pairs
+// (R, cn), R <= cn, in row-major order and within a pair by row offset;
+// C * nch (nch + 1) / 2 items per point (rows beyond n in the last chunk row
+// are empty items).  A block holds `ppb` points with `tpp` threads each; a
+// point's items are dealt round-robin to its threads.
+__device__ __forceinline__ void sym_item(int k, int C, int nch, int &i, int &cn)
+{
+    int b = k / C;
+    const int rho = k - b * C;
+    int R = 0, cnt = nch;
+    while (b >= cnt) {
+        b -= cnt;
+        ++R;
+        --cnt;
+    }
+    i = R * C + rho;
+    cn = R + b;
+}
+
+// Shared-memory bytes of the staged chunk matrix of one point (HVP): n rows
+// of n+1 (padded against bank conflicts on column reads).
+template <typename T>
+__host__ __device__ inline size_t sym_hs_bytes(int n)
+{
+    return (size_t)n * (n + 1) * sizeof(T);
+}
+
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+__global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n;
+    const int ppb = a.maxpts;  // points per block
+    const int tpp = a.tpp;     // threads per point
+    const Smem<T> L = smem_layout<T>(FN, HVP, n, ppb, a.mt);
+    Job job;
+    job.x = a.x;
+    job.v = a.v;
+    job.out = a.out;
+    job.A = a.A;
+    job.B = a.B;
+    job.npoints = a.batch;
+    job.row0 = 0;
+    job.n = n;
+    job.nch = a.nch;
+    job.tpr = 1;
+    job.maxpts = ppb;
+    job.mt = a.mt;
+    job.ld = a.ld;
+    ContigPoints pm{a.E, n};
+
+    const long long p0 = (long long)blockIdx.x * ppb;
+    const int npts = (int)min((long long)ppb, a.batch - p0);
+    point_prologue<T, IO, FN, HVP>(job, pm, smem_raw, L, p0, npts);
+
+    const int tid = threadIdx.x;
+    const int q = tid / tpp, t = tid - q * tpp;
+    const bool active = q < npts;
+    const long long p = p0 + (active ? q : 0);
+    const PointTables<T> pt(smem_raw, L, active ? q : 0, n);
+    T *Hs = reinterpret_cast<T *>(smem_raw + align_up(L.total, 16)) + (size_t)(active ? q : 0) * n * (n + 1);
+
+    const int nch = a.nch;
+    const int items = C * nch * (nch + 1) / 2;
+    const int iters = (items + tpp - 1) / tpp;
+    for (int it = 0; it < iters; ++it) {
+        const int k = t + it * tpp;
+        int i = 0, cn = 0;
+        bool has = active && k < items;
+        if (has) {
+            sym_item(k, C, nch, i, cn);
+            has = i < n;
+        }
+        if (FN != FN_FP && !has) continue;
+        const int cstart = cn * C;
+        const HD<T, C> f = row_chunk<T, C, FN, MB, true>(job, smem_raw, L, pt, i, cstart, has, it == 0);
+        if (!has) continue;
+        if constexpr (HVP) {
+#pragma unroll
+            for (int l = 0; l < C; ++l)
+                if (cstart + l < n) Hs[(size_t)i * (n + 1) + cstart + l] = f.h[l];
+        } else {
+            IO *H = reinterpret_cast<IO *>(a.out) + (size_t)p * n * n;
+            const bool mirror = cn > i / C;
+#pragma unroll
+            for (int l = 0; l < C; ++l) {
+                const int j = cstart + l;
+                if (j < n) {
+                    H[(size_t)i * n + j] = (IO)f.h[l];
+                    if (mirror) H[(size_t)j * n + i] = (IO)f.h[l];
+                }
+            }
+        }
+    }
+
+    if constexpr (HVP) {
+        // r_s = sum_j H_sj v_j over the staged chunks: entries right of row
+        // s's diagonal chunk from row s, entries left of it from column s
+        // (H_sj = H_js), so every off-diagonal-chunk entry serves both r_i and
+        // r_s as in Alg. 8.
+        __syncthreads();
+        if (active) {
+            const T *Hq = Hs;
+            IO *O = reinterpret_cast<IO *>(a.out) + (size_t)p * n;
+            for (int srow = t; srow < n; srow += tpp) {
+                const int dstart = (srow / C) * C;
+                if constexpr (IsComp<T>::value) {
+                    CSum d{0.f, 0.f};
+                    for (int j = 0; j < dstart; ++j) cdot_add(d, Hq[(size_t)j * (n + 1) + srow], pt.v[j]);
+                    for (int j = dstart; j < n; ++j) cdot_add(d, Hq[(size_t)srow * (n + 1) + j], pt.v[j]);
+                    O[srow] = (IO)csum_value(d);
+                } else {
+                    T d = T(0);
+                    for (int j = 0; j < dstart; ++j) d = fma_(Hq[(size_t)j * (n + 1) + srow], pt.v[j], d);
+                    for (int j = dstart; j < n; ++j) d = fma_(Hq[(size_t)srow * (n + 1) + j], pt.v[j], d);
+                    O[srow] = (IO)d;
+                }
+            }
+        }
+    }
+}
+
+// Host-side launch helpers: compute the layout, opt into large dynamic
+// shared memory once per (kernel, device), launch, report the error.
+template <typename K>
+cudaError_t opt_in_smem(K kern, size_t bytes, int *configured)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (configured[dev] < (int)bytes) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        configured[dev] = (int)bytes;
+    }
+    return cudaSuccess;
+}
+
 template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 cudaError_t launch_sweep(SweepArgs a, int block_threads, cudaStream_t stream)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
     auto kern = sweep_kernel<T, IO, C, FN, HVP, MB>;
-    if (L.total > 48 * 1024) {
-        static int configured[64] = {0};
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (dev < 0 || dev >= 64) dev = 0;
-        if (configured[dev] < (int)L.total) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-            if (e != cudaSuccess) return e;
-            configured[dev] = (int)L.total;
-        }
-    }
+    static int configured[64] = {0};
+    cudaError_t e = opt_in_smem(kern, L.total, configured);
+    if (e != cudaSuccess) return e;
     const long long threads = a.batch * (long long)a.tpp;
     const long long blocks = (threads + block_threads - 1) / block_threads;
     kern<<<(unsigned)blocks, block_threads, L.total, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Symmetric launch: a.maxpts = points per block, a.tpp = threads per point.
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+size_t sym_smem_bytes(const SweepArgs &a)
+{
+    const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
+    return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n) : 0);
+}
+
+template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+cudaError_t launch_sym(SweepArgs a, cudaStream_t stream)
+{
+    const size_t bytes = sym_smem_bytes<T, IO, C, FN, HVP, MB>(a);
+    auto kern = sym_kernel<T, IO, C, FN, HVP, MB>;
+    static int configured[64] = {0};
+    cudaError_t e = opt_in_smem(kern, bytes, configured);
+    if (e != cudaSuccess) return e;
+    const long long blocks = (a.batch + a.maxpts - 1) / a.maxpts;
+    kern<<<(unsigned)blocks, a.maxpts * a.tpp, bytes, stream>>>(a);
     return cudaGetLastError();
 }
 

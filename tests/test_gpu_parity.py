@@ -138,3 +138,56 @@ def test_kernel_info_and_peak():
     f64 = cf.chessfad_peak_flops(cf.FP64)
     assert 1e13 < f32 < 2e14
     assert 1e11 < f64 < f32
+
+
+# ------------------------------------------------------------------ symmetric method
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("c", CHUNKS)
+def test_symmetric_every_chunk(fn, prec, c):
+    """SC-HESS-VEC (Alg. 8) and SCHUNK-HESS (Alg. 6) against the oracle, n = 19
+    (ragged last chunk and last chunk row)."""
+    d = Dev(W.make_batch(fn, 19, 75, seed=300 + c), prec)
+    for tpp in (32, 64):
+        cfg = cf.Config(c, 0, 0, cf.SYMMETRIC, tpp)
+        e = hvp_err(d, d.hvp(cfg=cfg))
+        assert e.max() <= BOUND[prec], (tpp, e.max())
+        e = hessian_err(d, d.hessian(cfg=cfg))
+        assert e.max() <= BOUND[prec], (tpp, e.max())
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [1, 2, 3, 16, 64, 128])
+def test_symmetric_sizes(fn, prec, n):
+    batch = 40 if n <= 64 else 6
+    d = Dev(W.make_batch(fn, n, batch, seed=400 + n), prec)
+    for c in (4, 16):
+        cfg = cf.Config(c, 0, 0, cf.SYMMETRIC, 0)
+        assert hvp_err(d, d.hvp(cfg=cfg)).max() <= BOUND[prec], c
+        assert hessian_err(d, d.hessian(cfg=cfg)).max() <= BOUND[prec], c
+
+
+def test_symmetric_limits():
+    import torch
+
+    # symmetric Hessian at n = 300 (no staging limit); symmetric HVP beyond
+    # the shared-memory limit is rejected with CHESSFAD_ERR_SIZE
+    d = Dev(W.make_batch(W.ROSENBROCK, 300, 2, seed=1), cf.FP64)
+    cfg = cf.Config(16, 0, 0, cf.SYMMETRIC, 128)
+    assert hessian_err(d, d.hessian(cfg=cfg)).max() <= BOUND[cf.FP64]
+    out = torch.empty_like(d.x)
+    assert cf.chessfad_hvp_config(W.ROSENBROCK, 300, 2, cfg, d.x, d.v, out, None, cf.FP64) == -2
+    d32 = Dev(W.make_batch(W.ACKLEY, 200, 3, seed=2), cf.FP32_COMP)
+    assert hvp_err(d32, d32.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC, 64))).max() <= BOUND[cf.FP32_COMP]
+
+
+def test_symmetric_deterministic_and_equal_to_plain_within_bound():
+    d = Dev(W.make_batch(W.ACKLEY, 64, 300, seed=6), cf.FP64)
+    cfg = cf.Config(8, 0, 0, cf.SYMMETRIC, 32)
+    a = d.hvp(cfg=cfg)
+    b = d.hvp(cfg=cfg)
+    assert np.array_equal(a, b)
+    p = d.hvp(cfg=cf.Config(8, 1, 256))
+    ref, hn = d.ref_hvp()
+    assert np.max(np.linalg.norm(a - p, axis=1) / (hn * np.linalg.norm(d.vh, axis=1))) <= 2e-12
