@@ -106,16 +106,19 @@ typedef struct {
  *                     two, 1..32); lane r of a row evaluates chunks r, r+tpr,
  *                     ... and the row sum is finished by warp shuffles
  *                     (Sec. VI, Fig. 2 does this through shared memory)
- *   block_threads     plain method: CTA size, multiple of 32, 32..256
  *   method            CHESSFAD_METHOD_PLAIN or CHESSFAD_METHOD_SYMMETRIC
+ *   block_threads     plain method: CTA size, multiple of 32, 32..256;
+ *                     symmetric method: the CTA holds
+ *                     block_threads / threads_per_point points (at least
+ *                     one; fewer when the staged chunks of an HVP do not fit
+ *                     shared memory)
  *   threads_per_point symmetric method: threads sharing one point's
- *                     (row, chunk) items, 32..256 power of two; a CTA holds
- *                     256 / threads_per_point points (fewer when the staged
- *                     chunk matrix of an HVP does not fit shared memory)
+ *                     (row, chunk) items, 32..256 power of two
  * Zero in any field means "default" (method 0 is the plain method).  The
- * symmetric HVP stages a point's chunks in shared memory, n (n+1) values per
- * point: it supports n up to 220 (FP32) / 155 (FP64) and returns
- * CHESSFAD_ERR_SIZE beyond; the symmetric Hessian has no such limit. */
+ * symmetric HVP stages a point's chunks on and above the diagonal chunks in
+ * shared memory (about n (n + C) / 2 values per point): it supports n up to
+ * about 280 (FP32) / 200 (FP64) and returns CHESSFAD_ERR_SIZE beyond; the
+ * symmetric Hessian has no such limit. */
 typedef struct {
     int csize;
     int threads_per_row;

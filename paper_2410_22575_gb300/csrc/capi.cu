@@ -165,7 +165,7 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
             default: return f64 ? smem_fp_f64_sym(c.csize, hvp, a) : smem_fp_f32c_sym(c.csize, hvp, a);
             }
         };
-        int ppb = (int)std::min<long long>(batch, 256 / c.threads_per_point);
+        int ppb = (int)std::min<long long>(batch, std::max(1, c.block_threads / c.threads_per_point));
         const size_t kBudget = 200 * 1024;
         while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
         if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
@@ -318,7 +318,9 @@ int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const v
         for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
             for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
         if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
-        for (int p : {32, 64, 128}) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_SYMMETRIC, p});
+        for (int p : {32, 64, 128})
+            for (int bt : {128, 256})
+                if (bt >= p) cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
     }
     for (const chessfad_config &cfg : cands) {
         if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {

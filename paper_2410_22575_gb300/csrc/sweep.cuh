@@ -672,12 +672,26 @@ __device__ __forceinline__ void sym_item(int k, int C, int nch, int &i, int &cn)
     cn = R + b;
 }
 
-// Shared-memory bytes of the staged chunk matrix of one point (HVP): n rows
-// of n+1 (padded against bank conflicts on column reads).
-template <typename T>
-__host__ __device__ inline size_t sym_hs_bytes(int n)
+// Staged chunk matrix of one point (HVP), compact: row i (chunk row
+// R = i / C, offset rho) keeps columns R*C .. n-1 plus one pad element, so rows
+// of a chunk row have an odd-friendly stride n - R*C + 1 and column reads
+// across lanes hit distinct banks.
+__host__ __device__ inline long long sym_hs_row(int i, int n, int C)
 {
-    return (size_t)n * (n + 1) * sizeof(T);
+    const long long R = i / C, rho = i - R * C;
+    return C * (R * (n + 1) - C * R * (R - 1) / 2) + rho * (n - R * C + 1);
+}
+
+__host__ __device__ inline long long sym_hs_elems(int n, int C)
+{
+    const long long nch = (n + C - 1) / C;
+    return C * (nch * (n + 1) - C * nch * (nch - 1) / 2);
+}
+
+template <typename T>
+__host__ __device__ inline size_t sym_hs_bytes(int n, int C)
+{
+    return align_up((size_t)sym_hs_elems(n, C) * sizeof(T), 16);
 }
 
 template <typename T, typename IO, int C, int FN, bool HVP, int MB>
@@ -713,7 +727,7 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
     const bool active = q < npts;
     const long long p = p0 + (active ? q : 0);
     const PointTables<T> pt(smem_raw, L, active ? q : 0, n);
-    T *Hs = reinterpret_cast<T *>(smem_raw + align_up(L.total, 16)) + (size_t)(active ? q : 0) * n * (n + 1);
+    T *Hs = reinterpret_cast<T *>(smem_raw + align_up(L.total, 16) + (size_t)(active ? q : 0) * sym_hs_bytes<T>(n, C));
 
     const int nch = a.nch;
     const int items = C * nch * (nch + 1) / 2;
@@ -731,9 +745,10 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
         const HD<T, C> f = row_chunk<T, C, FN, MB, true>(job, smem_raw, L, pt, i, cstart, has, it == 0);
         if (!has) continue;
         if constexpr (HVP) {
+            T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
 #pragma unroll
             for (int l = 0; l < C; ++l)
-                if (cstart + l < n) Hs[(size_t)i * (n + 1) + cstart + l] = f.h[l];
+                if (cstart + l < n) hrow[cstart + l] = f.h[l];
         } else {
             IO *H = reinterpret_cast<IO *>(a.out) + (size_t)p * n * n;
             const bool mirror = cn > i / C;
@@ -759,15 +774,16 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
             IO *O = reinterpret_cast<IO *>(a.out) + (size_t)p * n;
             for (int srow = t; srow < n; srow += tpp) {
                 const int dstart = (srow / C) * C;
+                const T *own = Hq + sym_hs_row(srow, n, C) - dstart;  // own[j], j >= dstart
                 if constexpr (IsComp<T>::value) {
                     CSum d{0.f, 0.f};
-                    for (int j = 0; j < dstart; ++j) cdot_add(d, Hq[(size_t)j * (n + 1) + srow], pt.v[j]);
-                    for (int j = dstart; j < n; ++j) cdot_add(d, Hq[(size_t)srow * (n + 1) + j], pt.v[j]);
+                    for (int j = 0; j < dstart; ++j) cdot_add(d, Hq[sym_hs_row(j, n, C) + srow - (j / C) * C], pt.v[j]);
+                    for (int j = dstart; j < n; ++j) cdot_add(d, own[j], pt.v[j]);
                     O[srow] = (IO)csum_value(d);
                 } else {
                     T d = T(0);
-                    for (int j = 0; j < dstart; ++j) d = fma_(Hq[(size_t)j * (n + 1) + srow], pt.v[j], d);
-                    for (int j = dstart; j < n; ++j) d = fma_(Hq[(size_t)srow * (n + 1) + j], pt.v[j], d);
+                    for (int j = 0; j < dstart; ++j) d = fma_(Hq[sym_hs_row(j, n, C) + srow - (j / C) * C], pt.v[j], d);
+                    for (int j = dstart; j < n; ++j) d = fma_(own[j], pt.v[j], d);
                     O[srow] = (IO)d;
                 }
             }
@@ -811,7 +827,7 @@ template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 size_t sym_smem_bytes(const SweepArgs &a)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
-    return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n) : 0);
+    return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n, C) : 0);
 }
 
 template <typename T, typename IO, int C, int FN, bool HVP, int MB>

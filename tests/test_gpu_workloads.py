@@ -46,3 +46,28 @@ def test_rosenbrock_n256_hessian_and_hvp(prec):
     for lo in range(0, 1024, 128):  # bounded host memory for the reference
         rows = slice(lo, lo + 128)
         assert hessian_err(d, H, rows).max() <= BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", [cf.FP32_COMP, cf.FP64])
+def test_ackley_n64_autotuned_launch(prec):
+    """The launch configuration the benchmark times: autotune (both methods),
+    then csize = 0, at the full size of the headline workload."""
+    import torch
+
+    d = Dev(W.workload("ackley_n64"), prec)
+    out = torch.empty_like(d.x)
+    cfg = cf.chessfad_autotune_hvp(W.ACKLEY, 64, d.x.shape[0], d.x, d.v, out, None, prec)
+    assert cfg.csize in (1, 2, 4, 8, 16, 32)
+    e = hvp_err(d, d.hvp(csize=0))
+    assert e.max() <= BOUND[prec], (cfg.as_dict(), e.max())
+    # the symmetric configuration the benchmark reports, explicitly
+    e = hvp_err(d, d.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC, 64)))
+    assert e.max() <= BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", [cf.FP32_COMP, cf.FP64])
+def test_symmetric_full_workloads(prec):
+    for name in ("rosenbrock_n16", "fletcher_powell_n32"):
+        d = Dev(W.workload(name), prec)
+        e = hvp_err(d, d.hvp(cfg=cf.Config(4, 0, 0, cf.SYMMETRIC, 32)))
+        assert e.max() <= BOUND[prec], (name, e.max())
