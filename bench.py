@@ -520,7 +520,7 @@ def kernel_only(args):
         keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
         params = cf.fp_params(*keep)
     if args.method == "symmetric":
-        cfg = cf.Config(args.csize, 0, 0, cf.SYMMETRIC, args.tpp)
+        cfg = cf.Config(args.csize, 0, args.block, cf.SYMMETRIC, args.tpp)
     else:
         cfg = cf.Config(args.csize, args.tpr, args.block)
     stream = torch.cuda.current_stream()
@@ -540,6 +540,65 @@ def kernel_only(args):
                       **cfg.as_dict(), "ms": ms, "hvp_per_s": b.batch / (min(ms) * 1e-3)}))
 
 
+def report(args):
+    """Per-workload table for the benchmark spec: HVP/s (and Hessians/s) for every
+    named workload in both precisions, autotuned over both methods, plus the
+    plain method at the workload's stated chunk size."""
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    rows = []
+
+    def timed(fn_call, reps):
+        fn_call()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn_call()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return min(ms)
+
+    for name in ("rosenbrock_n16", "ackley_n64", "fletcher_powell_n32", "rosenbrock_n256"):
+        b = W.workload(name)
+        keep, params = [], None
+        if b.fn == W.FLETCHER_POWELL:
+            keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
+            params = cf.fp_params(*keep)
+        for prec, dt in ((cf.FP32_COMP, torch.float32), (cf.FP64, torch.float64)):
+            x = torch.tensor(b.x, dtype=dt, device="cuda")
+            v = torch.tensor(b.v, dtype=dt, device="cuda")
+            out = torch.empty_like(x)
+            reps = 5 if prec == cf.FP32_COMP else 2
+            cfg = cf.chessfad_autotune_hvp(b.fn, b.n, b.batch, x, v, out, params, prec)
+            t = timed(lambda: cf.chessfad_hvp(b.fn, b.n, b.batch, 0, x, v, out, params, prec), reps)
+            row = {"workload": name, "precision": "fp64" if prec == cf.FP64 else "fp32_comp",
+                   "tuned": cfg.as_dict(), "hvp_per_s": b.batch / (t * 1e-3), "ms": t}
+            c0 = 4 if name == "rosenbrock_n16" else cfg.csize
+            plain = cf.Config(c0, 1, 256)
+            t = timed(lambda: cf.chessfad_hvp_config(b.fn, b.n, b.batch, plain, x, v, out, params, prec), reps)
+            row["plain_c%d_hvp_per_s" % c0] = b.batch / (t * 1e-3)
+            if name in ("rosenbrock_n16", "rosenbrock_n256"):
+                H = torch.empty((b.batch, b.n, b.n), dtype=dt, device="cuda")
+                best = None
+                for hc in (cf.Config(c0, 1, 256), cf.Config(c0, 0, 256, cf.SYMMETRIC, 64)):
+                    t = timed(lambda: cf.chessfad_hessian_config(b.fn, b.n, b.batch, hc, x, H, params, prec), reps)
+                    if best is None or t < best[0]:
+                        best = (t, hc.as_dict())
+                row["hessians_per_s"] = b.batch / (best[0] * 1e-3)
+                row["hessian_cfg"] = best[1]
+                del H
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -552,6 +611,7 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the 100000-request uneven batch")
     ap.add_argument("--ragged-steps", type=int, default=1)
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
+    ap.add_argument("--report", action="store_true", help="per-workload table (all named workloads)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fn", type=int, default=None, help="kernel-only: function id instead of a named workload")
     ap.add_argument("--n", type=int, default=64)
@@ -566,7 +626,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and not args.kernel_only:
         args.warmup = 3
-    if args.kernel_only:
+    if args.report:
+        report(args)
+    elif args.kernel_only:
         kernel_only(args)
     elif args.impl == "reference":
         reference_arm(args)

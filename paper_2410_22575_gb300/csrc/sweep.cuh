@@ -71,8 +71,10 @@ __host__ __device__ inline Smem<T> smem_layout(int fn, bool hvp, int n, int maxp
     s.vs = off; if (hvp) off = align_up(off + pn * sizeof(T), 16);
     s.t1 = s.t2 = s.sc = s.res = s.dsin = s.dcos = s.at = s.bt = off;
     if (fn == FN_ACKLEY) {
-        s.t1 = off; off = align_up(off + pn * sizeof(T), 16);
-        s.t2 = off; off = align_up(off + pn * sizeof(T), 16);
+        // {x_k, phi'_k, phi''_k, pad} per variable, each point's n entries
+        // stored twice so a walk that wraps past n stays contiguous.
+        s.t1 = off; off = align_up(off + 2 * pn * 4 * sizeof(T), 16);
+        s.t2 = s.t1;
         s.sc = off; off = align_up(off + (size_t)maxpts * kAckScal * sizeof(T), 16);
     } else if (fn == FN_FP) {
         s.t1 = off; off = align_up(off + pn * sizeof(T), 16);    // sin x_j
@@ -248,6 +250,12 @@ __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, i
     return acc.value();
 }
 
+// One Ackley table entry: x_k and the derivatives of cos(2 pi t) at x_k.
+template <typename T>
+struct alignas(16) AckEnt {
+    T x, d1, d2, pad;
+};
+
 // Ackley on hDuals.  S = sum y_k^2 and Cs = sum cos(2 pi y_k) are accumulated
 // in the sweep for their derivative components; their value components are
 // the per-point FP64 sums from the table.  Each derivative component of S and
@@ -255,17 +263,51 @@ __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, i
 // a nonzero d/dx only for k == i or k in the chunk), so these sums are exact
 // up to that term's own rounding and need no compensation.
 template <typename T, int C, bool kRemap>
-__device__ __forceinline__ HD<T, C> ackley_sweep(const T *__restrict__ xs, const T *__restrict__ dcos1,
-                                                 const T *__restrict__ dcos2, const T *__restrict__ sc, int n,
+__device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ tab, const T *__restrict__ sc, int n,
                                                  int i, int cstart)
 {
     HD<T, C> S = hzero<T, C>();
     HD<T, C> Cs = hzero<T, C>();
-    for_each_seed<T, C, 16, kRemap>(xs, n, i, cstart, [&](int k, const HD<T, C> &y) {
+    // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
+    auto term = [&](const AckEnt<T> &e, const HD<T, C> &y) {
         S = hfma(y, y, S);
-        // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
-        add_unary<false>(Cs, y, T(0), dcos1[k], dcos2[k]);
-    });
+        add_unary<false>(Cs, y, T(0), e.d1, e.d2);
+    };
+    const int lo = min(cstart, n), hi = min(cstart + C, n);
+    if constexpr (kRemap) {
+        // The variables after the chunk, then (wrapping, on the table's second
+        // copy) those before it: one pointer, uniform trip count n - C.
+        const AckEnt<T> *p = tab + hi;
+        const AckEnt<T> *prow = tab + (i >= hi ? i : i + n);
+        const int nout = n - (hi - lo);
+        for (int kk = 0; kk < nout; ++kk, ++p) {
+            const AckEnt<T> e = *p;
+            term(e, seed_at<T, C, -1>(e.x, p == prow));
+        }
+    } else {
+        for (int k = 0; k < lo; ++k) {
+            const AckEnt<T> e = tab[k];
+            term(e, seed_at<T, C, -1>(e.x, k == i));
+        }
+        for (int k = hi; k < n; ++k) {
+            const AckEnt<T> e = tab[k];
+            term(e, seed_at<T, C, -1>(e.x, k == i));
+        }
+    }
+    if constexpr (Unroll<C, 16>::value) {
+        StaticFor<0, C>::run([&](auto P) {
+            const int k = cstart + P.value;
+            if (k < n) {
+                const AckEnt<T> e = tab[k];
+                term(e, seed_at<T, C, P.value>(e.x, k == i));
+            }
+        });
+    } else {
+        for (int k = lo; k < hi; ++k) {
+            const AckEnt<T> e = tab[k];
+            term(e, seed<T, C>(e.x, k, i, cstart));
+        }
+    }
     S.v = sc[0];   // sum x_k^2        (FP64 island)
     Cs.v = sc[1];  // sum cos(2 pi x_k) (FP64 island)
     const T inv_n = sc[2];
@@ -338,8 +380,7 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
     __syncthreads();
 
     if (FN == FN_ACKLEY) {
-        T *t1 = reinterpret_cast<T *>(smem_raw + L.t1);
-        T *t2 = reinterpret_cast<T *>(smem_raw + L.t2);
+        AckEnt<T> *tab = reinterpret_cast<AckEnt<T> *>(smem_raw + L.t1);
         T *sc = reinterpret_cast<T *>(smem_raw + L.sc);
         const int cnt = npts * n;
         for (int e = tid; e < cnt; e += blockDim.x) {
@@ -355,8 +396,14 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
                 s = (T)sf;
                 c = (T)cf;
             }
-            t1[e] = T(-2.0 * CUDART_PI) * s;
-            t2[e] = T(-4.0 * CUDART_PI * CUDART_PI) * c;
+            AckEnt<T> ent;
+            ent.x = xs[e];
+            ent.d1 = T(-2.0 * CUDART_PI) * s;
+            ent.d2 = T(-4.0 * CUDART_PI * CUDART_PI) * c;
+            ent.pad = T(0);
+            const int q = e / n, k = e - q * n;
+            tab[2 * q * n + k] = ent;
+            tab[2 * q * n + n + k] = ent;
         }
         __syncthreads();
         // One warp per point: S = sum x^2 and C = sum cos(2 pi x) in FP64.
@@ -366,7 +413,7 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
             for (int k = lane; k < n; k += 32) {
                 const double xv = (double)xs[q * n + k];
                 S = fma(xv, xv, S);
-                Cv += (double)t2[q * n + k] * (-1.0 / (4.0 * CUDART_PI * CUDART_PI));
+                Cv += (double)tab[2 * q * n + k].d2 * (-1.0 / (4.0 * CUDART_PI * CUDART_PI));
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
@@ -510,12 +557,14 @@ __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_r
 template <typename T>
 struct PointTables {
     const T *x, *v, *t1, *t2, *sc, *res;
+    const AckEnt<T> *ack;
     __device__ __forceinline__ PointTables(unsigned char *smem_raw, const Smem<T> &L, int q, int n)
     {
         x = reinterpret_cast<const T *>(smem_raw + L.xs) + q * n;
         v = reinterpret_cast<const T *>(smem_raw + L.vs) + q * n;
         t1 = reinterpret_cast<const T *>(smem_raw + L.t1) + q * n;
         t2 = reinterpret_cast<const T *>(smem_raw + L.t2) + q * n;
+        ack = reinterpret_cast<const AckEnt<T> *>(smem_raw + L.t1) + 2 * q * n;
         sc = reinterpret_cast<const T *>(smem_raw + L.sc) + q * kAckScal;
         res = reinterpret_cast<const T *>(smem_raw + L.res) + q * n;
     }
@@ -532,7 +581,7 @@ __device__ __forceinline__ HD<T, C> row_chunk(const Job &a, unsigned char *smem_
         if (has) return rosenbrock_sweep<T, C, kRemap>(pt.x, a.n, i, cstart);
         return hzero<T, C>();
     } else if constexpr (FN == FN_ACKLEY) {
-        if (has) return ackley_sweep<T, C, kRemap>(pt.x, pt.t1, pt.t2, pt.sc, a.n, i, cstart);
+        if (has) return ackley_sweep<T, C, kRemap>(pt.ack, pt.sc, a.n, i, cstart);
         return hzero<T, C>();
     } else {
         return fp_sweep<T, C, MB, kRemap>(a, smem_raw, L, pt.x, pt.t1, pt.t2, pt.res, i, cstart, has, reload);
