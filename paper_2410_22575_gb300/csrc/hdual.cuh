@@ -55,35 +55,55 @@ __device__ __forceinline__ HD<T, C> hzero()
 // CHUNK-INIT (Alg. 4) for one variable k, generated on the fly instead of
 // materialising y[n]: <x_k, [k == i], e_{k - cstart} if k is in the chunk, 0>.
 template <typename T, int C>
-__device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart)
+__device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart, T z)
 {
     HD<T, C> y;
     y.v = xk;
-    y.d1 = (k == i) ? T(1) : T(0);
+    y.d1 = (k == i) ? T(1) : z;
     const int d = k - cstart;
 #pragma unroll
     for (int l = 0; l < C; ++l) {
-        y.g[l] = (d == l) ? T(1) : T(0);
-        y.h[l] = T(0);
+        y.g[l] = (d == l) ? T(1) : z;
+        y.h[l] = z;
     }
     return y;
 }
 
+// A zero the compiler cannot see through.  Seeds built from it keep the
+// dense semantics of the method: every product with a seed zero is executed
+// (as in a library whose seeds are runtime values), never folded away.
+template <typename T>
+__device__ __forceinline__ T opaque_zero();
+template <>
+__device__ __forceinline__ float opaque_zero<float>()
+{
+    float z;
+    asm volatile("mov.b32 %0, 0;" : "=f"(z));
+    return z;
+}
+template <>
+__device__ __forceinline__ double opaque_zero<double>()
+{
+    double z;
+    asm volatile("mov.b64 %0, 0;" : "=d"(z));
+    return z;
+}
+
 // CHUNK-INIT seeds with the chunk position known at compile time: variable
 // k with chunk offset P = k - cstart (P outside [0, C) for variables outside
-// the chunk).  With P a constant the g part is a constant unit or zero
-// vector and costs no instructions; the arithmetic that consumes it is
-// unchanged (x * 0 cannot be folded away under IEEE rules).
+// the chunk).  With P a constant the seed needs no per-component selects; its
+// ones are literal (x * 1 is exact) and its zeros are the opaque zero z, so the
+// arithmetic that consumes the seed is the full dense rule.
 template <typename T, int C, int P>
-__device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row)
+__device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row, T z)
 {
     HD<T, C> y;
     y.v = xk;
-    y.d1 = is_row ? T(1) : T(0);
+    y.d1 = is_row ? T(1) : z;
 #pragma unroll
     for (int l = 0; l < C; ++l) {
-        y.g[l] = (l == P) ? T(1) : T(0);
-        y.h[l] = T(0);
+        y.g[l] = (l == P) ? T(1) : z;
+        y.h[l] = z;
     }
     return y;
 }
@@ -205,6 +225,19 @@ __device__ __forceinline__ void sfma_unary(HD<T, C> &acc, T s, const HD<T, C> &a
     for (int l = 0; l < C; ++l) {
         acc.g[l] = fma_(sd, a.g[l], acc.g[l]);
         acc.h[l] = fma_(sd, a.h[l], fma_(q, a.g[l], acc.h[l]));
+    }
+}
+
+// acc + s * u, componentwise; the value component only when kValue.
+template <bool kValue, typename T, int C>
+__device__ __forceinline__ void sfma(HD<T, C> &acc, T s, const HD<T, C> &a)
+{
+    if (kValue) acc.v = fma_(s, a.v, acc.v);
+    acc.d1 = fma_(s, a.d1, acc.d1);
+#pragma unroll
+    for (int l = 0; l < C; ++l) {
+        acc.g[l] = fma_(s, a.g[l], acc.g[l]);
+        acc.h[l] = fma_(s, a.h[l], acc.h[l]);
     }
 }
 

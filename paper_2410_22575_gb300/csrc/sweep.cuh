@@ -174,28 +174,29 @@ struct StaticFor {
 template <typename T, int C, int LIMIT, bool kRemap, typename F>
 __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
+    const T z = opaque_zero<T>();
     const int lo = min(cstart, n), hi = min(cstart + C, n);
     auto chunk = [&]() {
         if constexpr (Unroll<C, LIMIT>::value) {
             StaticFor<0, C>::run([&](auto P) {
                 const int k = cstart + P.value;
-                if (k < n) f(k, seed_at<T, C, P.value>(xs[k], k == i));
+                if (k < n) f(k, seed_at<T, C, P.value>(xs[k], k == i, z));
             });
         } else {
-            for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart));
+            for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart, z));
         }
     };
     if constexpr (kRemap) {
         const int nout = n - (hi - lo);
         for (int kk = 0; kk < nout; ++kk) {
             const int k = kk < lo ? kk : kk + (hi - lo);
-            f(k, seed_at<T, C, -1>(xs[k], k == i));
+            f(k, seed_at<T, C, -1>(xs[k], k == i, z));
         }
         chunk();
     } else {
-        for (int k = 0; k < lo; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
+        for (int k = 0; k < lo; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i, z));
         chunk();
-        for (int k = hi; k < n; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i));
+        for (int k = hi; k < n; ++k) f(k, seed_at<T, C, -1>(xs[k], k == i, z));
     }
 }
 
@@ -205,10 +206,11 @@ __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, i
 template <typename T, int C, int LIMIT, bool kRemap, typename F>
 __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
+    const T z = opaque_zero<T>();
     const int t0 = max(cstart - 1, 0);
     const int t1 = max(t0, min(cstart + C, n - 1));
     auto outside = [&](int k) {
-        f(seed_at<T, C, -1>(xs[k], k == i), seed_at<T, C, -1>(xs[k + 1], k + 1 == i));
+        f(seed_at<T, C, -1>(xs[k], k == i, z), seed_at<T, C, -1>(xs[k + 1], k + 1 == i, z));
     };
     auto touching = [&]() {
         if constexpr (Unroll<C, LIMIT>::value) {
@@ -216,11 +218,11 @@ __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, i
                 constexpr int t = decltype(Q)::value - 1;
                 const int k = cstart + t;
                 if (k >= 0 && k + 1 < n)
-                    f(seed_at<T, C, t>(xs[k], k == i), seed_at<T, C, t + 1>(xs[k + 1], k + 1 == i));
+                    f(seed_at<T, C, t>(xs[k], k == i, z), seed_at<T, C, t + 1>(xs[k + 1], k + 1 == i, z));
             });
         } else {
             for (int k = t0; k < t1; ++k)
-                f(seed<T, C>(xs[k], k, i, cstart), seed<T, C>(xs[k + 1], k + 1, i, cstart));
+                f(seed<T, C>(xs[k], k, i, cstart, z), seed<T, C>(xs[k + 1], k + 1, i, cstart, z));
         }
     };
     if constexpr (kRemap) {
@@ -266,6 +268,7 @@ template <typename T, int C, bool kRemap>
 __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ tab, const T *__restrict__ sc, int n,
                                                  int i, int cstart)
 {
+    const T z = opaque_zero<T>();
     HD<T, C> S = hzero<T, C>();
     HD<T, C> Cs = hzero<T, C>();
     // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
@@ -282,16 +285,16 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
         const int nout = n - (hi - lo);
         for (int kk = 0; kk < nout; ++kk, ++p) {
             const AckEnt<T> e = *p;
-            term(e, seed_at<T, C, -1>(e.x, p == prow));
+            term(e, seed_at<T, C, -1>(e.x, p == prow, z));
         }
     } else {
         for (int k = 0; k < lo; ++k) {
             const AckEnt<T> e = tab[k];
-            term(e, seed_at<T, C, -1>(e.x, k == i));
+            term(e, seed_at<T, C, -1>(e.x, k == i, z));
         }
         for (int k = hi; k < n; ++k) {
             const AckEnt<T> e = tab[k];
-            term(e, seed_at<T, C, -1>(e.x, k == i));
+            term(e, seed_at<T, C, -1>(e.x, k == i, z));
         }
     }
     if constexpr (Unroll<C, 16>::value) {
@@ -299,13 +302,13 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
             const int k = cstart + P.value;
             if (k < n) {
                 const AckEnt<T> e = tab[k];
-                term(e, seed_at<T, C, P.value>(e.x, k == i));
+                term(e, seed_at<T, C, P.value>(e.x, k == i, z));
             }
         });
     } else {
         for (int k = lo; k < hi; ++k) {
             const AckEnt<T> e = tab[k];
-            term(e, seed<T, C>(e.x, k, i, cstart));
+            term(e, seed<T, C>(e.x, k, i, cstart, z));
         }
     }
     S.v = sc[0];   // sum x_k^2        (FP64 island)
@@ -534,10 +537,14 @@ __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_r
                 const T sj = ts[jv], cj = tc[jv];
                 const T *ar = At + jv * mt + (mb - m0);
                 const T *br = Bt + jv * mt + (mb - m0);
+                // sin(y_j) and cos(y_j) once per j (unary rule), then
+                // s_m += A_mj sin(y_j) + B_mj cos(y_j) for the MB rows.
+                const HD<T, C> sy = unary(y, sj, cj, -sj);
+                const HD<T, C> cy = unary(y, cj, -sj, -cj);
 #pragma unroll
                 for (int u = 0; u < MB; ++u) {
-                    sfma_unary<false>(s[u], ar[u], y, sj, cj, -sj);   // + A_mj sin y_j
-                    sfma_unary<false>(s[u], br[u], y, cj, -sj, -cj);  // + B_mj cos y_j
+                    sfma<false>(s[u], ar[u], sy);
+                    sfma<false>(s[u], br[u], cy);
                 }
             });
 #pragma unroll
