@@ -115,20 +115,51 @@ struct TermSum<T, C, false> {
     __device__ __forceinline__ HD<T, C> value() const { return s; }
 };
 
+// Compensated FP32: blocked Sum2.  Terms are fused (FMA) into a plain FP32
+// block partial; every kSumBlock terms the partial is added into the
+// compensated pair (sum, error) with TwoSum, and value() adds the last
+// partial and the error.  Each block partial carries at most
+// (kSumBlock - 1) u of its own terms' magnitude in rounding error; the
+// compensated pair then adds the partials with twice-working-precision
+// accuracy (Ogita, Rump & Oishi, Sum2 over the partials).
+constexpr int kSumBlock = 8;
+
 template <int C>
 struct TermSum<float, C, true> {
     CHD<C> s;
-    __device__ __forceinline__ void init() { chd_zero(s); }
+    HD<float, C> blk;
+    int cnt;
+    __device__ __forceinline__ void init()
+    {
+        chd_zero(s);
+        blk = hzero<float, C>();
+        cnt = 0;
+    }
+    __device__ __forceinline__ void step()
+    {
+        if (++cnt == kSumBlock) {
+            chd_add(s, blk);
+            blk = hzero<float, C>();
+            cnt = 0;
+        }
+    }
     __device__ __forceinline__ void add_prod2(const HD<float, C> &a, const HD<float, C> &b, const HD<float, C> &c,
                                               const HD<float, C> &d)
     {
-        chd_add(s, hfma(a, b, hmul(c, d)));
+        blk = hfma(a, b, hfma(c, d, blk));
+        step();
     }
     __device__ __forceinline__ void add_prod(const HD<float, C> &a, const HD<float, C> &b)
     {
-        chd_add(s, hmul(a, b));
+        blk = hfma(a, b, blk);
+        step();
     }
-    __device__ __forceinline__ HD<float, C> value() const { return chd_value(s); }
+    __device__ __forceinline__ HD<float, C> value() const
+    {
+        CHD<C> t = s;
+        chd_add(t, blk);
+        return chd_value(t);
+    }
 };
 
 template <typename T>
