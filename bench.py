@@ -599,6 +599,87 @@ def report(args):
     return rows
 
 
+def cpu_baseline_report(args):
+    """The CPU-baseline leg for every named workload: the oracle's CHESS-VEC
+    (Alg. 7, FP64, OpenMP over points) on a timed prefix of the batch and the
+    closed-form oracle on the whole batch, on this host's cores."""
+    import oracle
+    from paper_2410_22575_gb300 import workloads as W
+
+    oracle.build()
+    for name, c in (("rosenbrock_n16", 4), ("ackley_n64", 8), ("fletcher_powell_n32", 4), ("rosenbrock_n256", 16)):
+        b = W.workload(name)
+        p = None if b.fp is None else oracle.FPParams(b.fp.A, b.fp.B, b.fp.E)
+        probe = 8
+        t0 = time.perf_counter()
+        oracle.chess_vec(b.fn, b.x[:probe], b.v[:probe], c, p)
+        dt = time.perf_counter() - t0
+        m = int(min(b.batch, max(probe, probe * args.cpu_seconds / 3 / max(dt, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.chess_vec(b.fn, b.x[:m], b.v[:m], c, p)
+        t_cv = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.hvp(b.fn, b.x, b.v, p)
+        t_cf = time.perf_counter() - t0
+        print(json.dumps({"workload": name, "cores": oracle.num_threads(), "chess_vec_c": c,
+                          "chess_vec_hvp_per_s": m / t_cv, "chess_vec_sample": m,
+                          "closed_form_hvp_per_s": b.batch / t_cf}), flush=True)
+
+
+def chunk_study(args):
+    """Measured best chunk size per (function, n, method) in compensated FP32
+    against the Sec. V operation-count model: for the plain method the
+    multiplication count (6 + 3/c) n^2 M falls with c (largest c best); for
+    the symmetric method (3/2) n (2n + 2c + n/c + 1) M is smallest at
+    c = sqrt(n/2)."""
+    import math
+
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    for fn in (W.ROSENBROCK, W.ACKLEY, W.FLETCHER_POWELL):
+        for n in (8, 16, 32, 64, 128):
+            budget = 2.0e11 if fn != W.FLETCHER_POWELL else 6.0e11
+            cost = n ** 3 if fn != W.FLETCHER_POWELL else n ** 4
+            batch = int(max(256, min(65536, budget / (20 * cost))))
+            b = W.make_batch(fn, n, batch, seed=100 + n)
+            keep, params = [], None
+            if fn == W.FLETCHER_POWELL:
+                keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
+                params = cf.fp_params(*keep)
+            x = torch.tensor(b.x, dtype=torch.float32, device="cuda")
+            v = torch.tensor(b.v, dtype=torch.float32, device="cuda")
+            out = torch.empty_like(x)
+            res = {}
+            for method in ("plain", "symmetric"):
+                for c in (1, 2, 4, 8, 16, 32):
+                    if c > max(1, 1 << (n - 1).bit_length()):
+                        continue
+                    cfg = (cf.Config(c, 1, 256) if method == "plain"
+                           else cf.Config(c, 0, 128, cf.SYMMETRIC, 32))
+                    if cf.chessfad_hvp_config(fn, n, batch, cfg, x, v, out, params, cf.FP32_COMP) != 0:
+                        continue
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    for _ in range(3):
+                        cf.chessfad_hvp_config(fn, n, batch, cfg, x, v, out, params, cf.FP32_COMP)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    res[(method, c)] = 3 * batch / (e0.elapsed_time(e1) * 1e-3)
+            for method in ("plain", "symmetric"):
+                cs = {c: r for (m, c), r in res.items() if m == method}
+                if not cs:
+                    continue
+                best = max(cs, key=cs.get)
+                print(json.dumps({"function": W.FN_NAMES[fn], "n": n, "method": method, "best_c": best,
+                                  "model_c": (max(cs) if method == "plain" else math.sqrt(n / 2)),
+                                  "hvp_per_s": {str(c): round(r) for c, r in sorted(cs.items())}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -612,6 +693,8 @@ def main():
     ap.add_argument("--ragged-steps", type=int, default=1)
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
     ap.add_argument("--report", action="store_true", help="per-workload table (all named workloads)")
+    ap.add_argument("--chunk-study", action="store_true", help="measured best chunk size vs the Sec. V model")
+    ap.add_argument("--cpu-report", action="store_true", help="CPU-baseline leg for every named workload")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fn", type=int, default=None, help="kernel-only: function id instead of a named workload")
     ap.add_argument("--n", type=int, default=64)
@@ -626,7 +709,11 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and not args.kernel_only:
         args.warmup = 3
-    if args.report:
+    if args.cpu_report:
+        cpu_baseline_report(args)
+    elif args.chunk_study:
+        chunk_study(args)
+    elif args.report:
         report(args)
     elif args.kernel_only:
         kernel_only(args)

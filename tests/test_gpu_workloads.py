@@ -71,3 +71,29 @@ def test_symmetric_full_workloads(prec):
         d = Dev(W.workload(name), prec)
         e = hvp_err(d, d.hvp(cfg=cf.Config(4, 0, 0, cf.SYMMETRIC, 32)))
         assert e.max() <= BOUND[prec], (name, e.max())
+
+
+def test_error_report_every_workload():
+    """Max / median normalised error of every named workload in both
+    precisions, in the autotuned configuration (both methods searched); the
+    bounds are asserted, and the table is written to the file named by
+    CHESSFAD_ERROR_REPORT when that variable is set."""
+    import json
+    import os
+
+    import torch
+
+    rows = []
+    for name in ("rosenbrock_n16", "ackley_n64", "fletcher_powell_n32", "rosenbrock_n256"):
+        for prec in (cf.FP32_COMP, cf.FP64):
+            d = Dev(W.workload(name), prec)
+            out = torch.empty_like(d.x)
+            cfg = cf.chessfad_autotune_hvp(d.b.fn, d.b.n, d.b.batch, d.x, d.v, out, d.params, prec)
+            e = hvp_err(d, d.hvp(csize=0))
+            assert e.max() <= BOUND[prec], (name, prec, e.max())
+            rows.append({"workload": name, "precision": "fp64" if prec == cf.FP64 else "fp32_comp",
+                         "config": cfg.as_dict(), "max": float(e.max()), "median": float(np.median(e))})
+    path = os.environ.get("CHESSFAD_ERROR_REPORT")
+    if path:
+        with open(path, "w") as f:
+            json.dump(rows, f, indent=1)
