@@ -245,6 +245,23 @@ def gpu_arm(args):
                 ent[mname] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t}
             sweep[str(c)] = ent
         res[prec]["sweep"] = sweep
+
+        # seed-sparse symmetric method (a different arithmetic: reported beside
+        # the headline, never as it)
+        sparse = {}
+        for c in (4, 8):
+            scfg = cf.Config(c, 0, 128, cf.SYMMETRIC_SPARSE, 64)
+
+            def sts(scfg=scfg):
+                st = cf.chessfad_hvp_config(fn, n, batch, scfg, x, v, out, None, prec, stream)
+                if st != 0:
+                    raise cf.ChessfadError(st, "chessfad_hvp")
+
+            k = max(1, min(5, steps))
+            m = timed_steps(sts, k, 1, stream, flush)
+            t = max_over_ranks(world, sum(m), dev) / k
+            sparse[str(c)] = {**scfg.as_dict(), "hvp_per_s": world * batch / (t * 1e-3), "ms": t}
+        res[prec]["sparse"] = sparse
         del x, v, out
 
     # ---- end to end: pinned host buffers -> device -> hvp -> host, FP32-comp
@@ -326,6 +343,9 @@ def gpu_arm(args):
                  "peak_tflops_derived": peak_fp64 / 1e12},
         "fp32_over_fp64": value / v64,
         "chunk_sweep": {"fp32_comp": f32["sweep"], "fp64": f64["sweep"]},
+        "seed_sparse": {"fp32_comp": f32["sparse"], "fp64": f64["sparse"],
+                        "method": "symmetric, seed-sparse propagation (skips variables whose seed has no "
+                                  "derivative part); equal to the dense result for finite inputs"},
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak_fp32, "traffic": traffic,
                      "flops_per_launch": flops_launch,
@@ -519,8 +539,9 @@ def kernel_only(args):
     if b.fn == W.FLETCHER_POWELL:
         keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
         params = cf.fp_params(*keep)
-    if args.method == "symmetric":
-        cfg = cf.Config(args.csize, 0, args.block, cf.SYMMETRIC, args.tpp)
+    if args.method in ("symmetric", "symmetric_sparse"):
+        m = cf.SYMMETRIC if args.method == "symmetric" else cf.SYMMETRIC_SPARSE
+        cfg = cf.Config(args.csize, 0, args.block, m, args.tpp)
     else:
         cfg = cf.Config(args.csize, args.tpr, args.block)
     stream = torch.cuda.current_stream()
@@ -704,7 +725,7 @@ def main():
     ap.add_argument("--csize", type=int, default=32)
     ap.add_argument("--tpr", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--method", choices=["plain", "symmetric"], default="plain")
+    ap.add_argument("--method", choices=["plain", "symmetric", "symmetric_sparse"], default="plain")
     ap.add_argument("--tpp", type=int, default=64, help="kernel-only, symmetric: threads per point")
     args = ap.parse_args()
     if args.warmup < 3 and not args.kernel_only:

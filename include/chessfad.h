@@ -99,6 +99,15 @@ typedef struct {
 #define CHESSFAD_METHOD_PLAIN 0     /* every chunk of every row: CHUNK-HESS (Alg. 5), CHESS-VEC (Alg. 7) */
 #define CHESSFAD_METHOD_SYMMETRIC 1 /* only chunks from the row's diagonal chunk on: SCHUNK-HESS (Alg. 6),
                                        SC-HESS-VEC (Alg. 8); about half the evaluations of f (Sec. V) */
+#define CHESSFAD_METHOD_SYMMETRIC_SPARSE 2 /* the symmetric method with seed-sparse propagation: an
+                                       evaluation of f visits only the variables whose CHUNK-INIT seed
+                                       has a nonzero derivative part (x_i and the chunk; for
+                                       Rosenbrock the terms touching them).  The others add to
+                                       value components only, which are per-point constants.  This
+                                       departs from the paper's dense arithmetic: the result equals
+                                       the dense one for finite inputs, but NaN/Inf in the skipped
+                                       variables does not reach the derivatives.  csize 4, 8 or 16;
+                                       never chosen by the autotuner. */
 
 /* Launch configuration of the (point, row, chunk) decomposition.
  *   csize             chunk size, 1..32 power of two
@@ -106,7 +115,7 @@ typedef struct {
  *                     two, 1..32); lane r of a row evaluates chunks r, r+tpr,
  *                     ... and the row sum is finished by warp shuffles
  *                     (Sec. VI, Fig. 2 does this through shared memory)
- *   method            CHESSFAD_METHOD_PLAIN or CHESSFAD_METHOD_SYMMETRIC
+ *   method            CHESSFAD_METHOD_PLAIN, _SYMMETRIC or _SYMMETRIC_SPARSE
  *   block_threads     plain method: CTA size, multiple of 32, 32..256;
  *                     symmetric method: the CTA holds
  *                     block_threads / threads_per_point points (at least

@@ -75,6 +75,8 @@ static chessfad_config resolve(int fn, int n, long long batch, int prec, const c
         if (c.threads_per_point == 0) c.threads_per_point = base.threads_per_point;
         if (!cfg || cfg->method == 0) c.method = base.method;
         c.csize = base.csize;
+        // the seed-sparse kernels exist for chunk sizes 4, 8 and 16 only
+        if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE) c.csize = std::min(16, std::max(4, c.csize));
     }
     if (c.threads_per_point == 0) c.threads_per_point = default_threads_per_point(n, batch);
     if (c.threads_per_row == 0 || c.block_threads == 0) {
@@ -104,7 +106,11 @@ static int check_config(const chessfad_config &c)
     const int t = c.threads_per_row;
     if (t < 1 || t > 32 || (t & (t - 1))) return CHESSFAD_ERR_CONFIG;
     if (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32) return CHESSFAD_ERR_CONFIG;
-    if (c.method != CHESSFAD_METHOD_PLAIN && c.method != CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_CONFIG;
+    if (c.method != CHESSFAD_METHOD_PLAIN && c.method != CHESSFAD_METHOD_SYMMETRIC &&
+        c.method != CHESSFAD_METHOD_SYMMETRIC_SPARSE)
+        return CHESSFAD_ERR_CONFIG;
+    if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE && c.csize != 4 && c.csize != 8 && c.csize != 16)
+        return CHESSFAD_ERR_CHUNK;
     const int p = c.threads_per_point;
     if (p < 32 || p > 256 || (p & (p - 1))) return CHESSFAD_ERR_CONFIG;
     return CHESSFAD_SUCCESS;
@@ -153,7 +159,9 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
     if (fn == CHESSFAD_FLETCHER_POWELL && a.mt % fp_mb(c.csize) != 0) return CHESSFAD_ERR_CONFIG;
     cudaError_t e = cudaErrorInvalidValue;
     const bool f64 = (prec == CHESSFAD_FP64);
-    if (c.method == CHESSFAD_METHOD_SYMMETRIC && !(!f64 && n == 1)) {
+    const bool sym = c.method == CHESSFAD_METHOD_SYMMETRIC || c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE;
+    if (sym && !(!f64 && n == 1)) {
+        const bool sparse = c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE;
         // Symmetric method: a.maxpts = points per block, a.tpp = threads per
         // point; as many points per CTA as shared memory allows (<= 200 KiB).
         a.tpp = c.threads_per_point;
@@ -170,16 +178,32 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
         if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
         a.maxpts = ppb;
-        switch (fn) {
-        case CHESSFAD_ROSENBROCK:
-            e = f64 ? launch_rosenbrock_f64_sym(c.csize, hvp, a, stream) : launch_rosenbrock_f32c_sym(c.csize, hvp, a, stream);
-            break;
-        case CHESSFAD_ACKLEY:
-            e = f64 ? launch_ackley_f64_sym(c.csize, hvp, a, stream) : launch_ackley_f32c_sym(c.csize, hvp, a, stream);
-            break;
-        case CHESSFAD_FLETCHER_POWELL:
-            e = f64 ? launch_fp_f64_sym(c.csize, hvp, a, stream) : launch_fp_f32c_sym(c.csize, hvp, a, stream);
-            break;
+        if (sparse) {
+            switch (fn) {
+            case CHESSFAD_ROSENBROCK:
+                e = f64 ? launch_rosenbrock_f64_sym_sparse(c.csize, hvp, a, stream)
+                        : launch_rosenbrock_f32c_sym_sparse(c.csize, hvp, a, stream);
+                break;
+            case CHESSFAD_ACKLEY:
+                e = f64 ? launch_ackley_f64_sym_sparse(c.csize, hvp, a, stream)
+                        : launch_ackley_f32c_sym_sparse(c.csize, hvp, a, stream);
+                break;
+            case CHESSFAD_FLETCHER_POWELL:
+                e = f64 ? launch_fp_f64_sym_sparse(c.csize, hvp, a, stream) : launch_fp_f32c_sym_sparse(c.csize, hvp, a, stream);
+                break;
+            }
+        } else {
+            switch (fn) {
+            case CHESSFAD_ROSENBROCK:
+                e = f64 ? launch_rosenbrock_f64_sym(c.csize, hvp, a, stream) : launch_rosenbrock_f32c_sym(c.csize, hvp, a, stream);
+                break;
+            case CHESSFAD_ACKLEY:
+                e = f64 ? launch_ackley_f64_sym(c.csize, hvp, a, stream) : launch_ackley_f32c_sym(c.csize, hvp, a, stream);
+                break;
+            case CHESSFAD_FLETCHER_POWELL:
+                e = f64 ? launch_fp_f64_sym(c.csize, hvp, a, stream) : launch_fp_f32c_sym(c.csize, hvp, a, stream);
+                break;
+            }
         }
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }

@@ -41,6 +41,16 @@ CHESSFAD_SYM(fp_f64);
 CHESSFAD_SYM(fp_f32c);
 #undef CHESSFAD_SYM
 
+// Symmetric method with seed-sparse propagation; C in {4, 8, 16}.
+#define CHESSFAD_SPARSE(name) cudaError_t launch_##name##_sym_sparse(int C, bool hvp, const SweepArgs &a, cudaStream_t stream)
+CHESSFAD_SPARSE(rosenbrock_f64);
+CHESSFAD_SPARSE(rosenbrock_f32c);
+CHESSFAD_SPARSE(ackley_f64);
+CHESSFAD_SPARSE(ackley_f32c);
+CHESSFAD_SPARSE(fp_f64);
+CHESSFAD_SPARSE(fp_f32c);
+#undef CHESSFAD_SPARSE
+
 // cudaFuncGetAttributes of the instantiation (registers, local memory).
 #define CHESSFAD_ATTR(name) cudaError_t name(int C, bool hvp, cudaFuncAttributes *fa)
 CHESSFAD_ATTR(attr_rosenbrock_f64);

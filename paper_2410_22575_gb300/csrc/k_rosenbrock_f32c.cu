@@ -85,4 +85,18 @@ size_t smem_rosenbrock_f32c_sym(int C, bool hvp, const SweepArgs &a)
     return 0;
 }
 
+// Symmetric method with seed-sparse propagation (chunk sizes 4, 8, 16).
+cudaError_t launch_rosenbrock_f32c_sym_sparse(int C, bool hvp, const SweepArgs &a, cudaStream_t s)
+{
+    switch (C) {
+    case 4: return hvp ? launch_sym<float, float, 4, FN_ROSENBROCK, true, fp_mb(4), true>(a, s)
+                       : launch_sym<float, float, 4, FN_ROSENBROCK, false, fp_mb(4), true>(a, s);
+    case 8: return hvp ? launch_sym<float, float, 8, FN_ROSENBROCK, true, fp_mb(8), true>(a, s)
+                       : launch_sym<float, float, 8, FN_ROSENBROCK, false, fp_mb(8), true>(a, s);
+    case 16: return hvp ? launch_sym<float, float, 16, FN_ROSENBROCK, true, fp_mb(16), true>(a, s)
+                        : launch_sym<float, float, 16, FN_ROSENBROCK, false, fp_mb(16), true>(a, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace chessfad

@@ -202,7 +202,7 @@ struct StaticFor {
 // in one loop of uniform trip count, then the chunk (lanes of a warp on
 // different chunks stay converged); otherwise three segments in ascending
 // order (cheapest when a warp's lanes share the chunk).
-template <typename T, int C, int LIMIT, bool kRemap, typename F>
+template <typename T, int C, int LIMIT, bool kRemap, bool kSparse = false, typename F>
 __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
     const T z = opaque_zero<T>();
@@ -217,7 +217,12 @@ __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, i
             for (int k = lo; k < hi; ++k) f(k, seed<T, C>(xs[k], k, i, cstart, z));
         }
     };
-    if constexpr (kRemap) {
+    if constexpr (kSparse) {
+        // Seed-sparse: only y_i and the chunk's variables carry nonzero
+        // derivatives; the others add to value components only.
+        chunk();
+        if (i < lo || i >= hi) f(i, seed_at<T, C, -1>(xs[i], true, z));
+    } else if constexpr (kRemap) {
         const int nout = n - (hi - lo);
         for (int kk = 0; kk < nout; ++kk) {
             const int k = kk < lo ? kk : kk + (hi - lo);
@@ -234,7 +239,7 @@ __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, i
 // f(y_k, y_{k+1}) for every k in 0 .. n-2 (functions whose terms couple
 // neighbours).  The pairs touching the chunk are k - cstart in [-1, C-1];
 // kRemap as for for_each_seed.
-template <typename T, int C, int LIMIT, bool kRemap, typename F>
+template <typename T, int C, int LIMIT, bool kRemap, bool kSparse = false, typename F>
 __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
     const T z = opaque_zero<T>();
@@ -256,7 +261,13 @@ __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, i
                 f(seed<T, C>(xs[k], k, i, cstart, z), seed<T, C>(xs[k + 1], k + 1, i, cstart, z));
         }
     };
-    if constexpr (kRemap) {
+    if constexpr (kSparse) {
+        // Seed-sparse: the pairs touching the chunk, and the pairs (i-1, i),
+        // (i, i+1) when they do not touch it.
+        touching();
+        if (i >= 1 && (i - 1 < t0 || i - 1 >= t1)) outside(i - 1);
+        if (i + 1 < n && (i < t0 || i >= t1)) outside(i);
+    } else if constexpr (kRemap) {
         const int nout = max(0, n - 1 - (t1 - t0));
         for (int kk = 0; kk < nout; ++kk) outside(kk < t0 ? kk : kk + (t1 - t0));
         touching();
@@ -269,12 +280,12 @@ __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, i
 
 // ------------------------------------------------------------------ functions
 // Rosenbrock, f = sum_{k<n-1} 100 (x_{k+1} - x_k^2)^2 + (1 - x_k)^2, on hDuals.
-template <typename T, int C, bool kRemap>
+template <typename T, int C, bool kRemap, bool kSparse>
 __device__ __forceinline__ HD<T, C> rosenbrock_sweep(const T *__restrict__ xs, int n, int i, int cstart)
 {
     TermSum<T, C, IsComp<T>::value> acc;
     acc.init();
-    for_each_pair<T, C, 8, kRemap>(xs, n, i, cstart, [&](const HD<T, C> &y0, const HD<T, C> &y1) {
+    for_each_pair<T, C, 8, kRemap, kSparse>(xs, n, i, cstart, [&](const HD<T, C> &y0, const HD<T, C> &y1) {
         const HD<T, C> d = hsub(y1, hmul(y0, y0));  // x_{k+1} - x_k^2
         const HD<T, C> w = smul(T(100), d);           // 100 (x_{k+1} - x_k^2)
         const HD<T, C> e = rsub(T(1), y0);            // 1 - x_k
@@ -295,7 +306,7 @@ struct alignas(16) AckEnt {
 // Cs receives at most one nonzero term under CHUNK-INIT seeding (y_k carries
 // a nonzero d/dx only for k == i or k in the chunk), so these sums are exact
 // up to that term's own rounding and need no compensation.
-template <typename T, int C, bool kRemap>
+template <typename T, int C, bool kRemap, bool kSparse>
 __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ tab, const T *__restrict__ sc, int n,
                                                  int i, int cstart)
 {
@@ -308,7 +319,14 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
         add_unary<false>(Cs, y, T(0), e.d1, e.d2);
     };
     const int lo = min(cstart, n), hi = min(cstart + C, n);
-    if constexpr (kRemap) {
+    if constexpr (kSparse) {
+        // Seed-sparse: besides the chunk (below) only y_i has a nonzero
+        // derivative part.
+        if (i < lo || i >= hi) {
+            const AckEnt<T> e = tab[i];
+            term(e, seed_at<T, C, -1>(e.x, true, z));
+        }
+    } else if constexpr (kRemap) {
         // The variables after the chunk, then (wrapping, on the table's second
         // copy) those before it: one pointer, uniform trip count n - C.
         const AckEnt<T> *p = tab + hi;
@@ -527,7 +545,7 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
 // tile loads are block-wide: every thread of the block makes the same calls
 // (threads without a sweep pass has = false); with a single tile the load
 // happens only when `reload` is set.
-template <typename T, int C, int MB, bool kRemap>
+template <typename T, int C, int MB, bool kRemap, bool kSparse>
 __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_raw, const Smem<T> &L, const T *xq,
                                              const T *ts, const T *tc, const T *res, int i, int cstart, bool has,
                                              bool reload)
@@ -564,7 +582,7 @@ __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_r
             HD<T, C> s[MB];
 #pragma unroll
             for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
-            for_each_seed<T, C, 16, kRemap>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
+            for_each_seed<T, C, 16, kRemap, kSparse>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
                 const T sj = ts[jv], cj = tc[jv];
                 const T *ar = At + jv * mt + (mb - m0);
                 const T *br = Bt + jv * mt + (mb - m0);
@@ -611,18 +629,18 @@ struct PointTables {
 // f's hDual for (row i, chunk at cstart) of a staged point.  Rosenbrock and
 // Ackley sweeps are per-thread; Fletcher-Powell's is block-uniform (see
 // fp_sweep), so every thread calls this with the same trip counts.
-template <typename T, int C, int FN, int MB, bool kRemap>
+template <typename T, int C, int FN, int MB, bool kRemap, bool kSparse = false>
 __device__ __forceinline__ HD<T, C> row_chunk(const Job &a, unsigned char *smem_raw, const Smem<T> &L,
                                               const PointTables<T> &pt, int i, int cstart, bool has, bool reload)
 {
     if constexpr (FN == FN_ROSENBROCK) {
-        if (has) return rosenbrock_sweep<T, C, kRemap>(pt.x, a.n, i, cstart);
+        if (has) return rosenbrock_sweep<T, C, kRemap, kSparse>(pt.x, a.n, i, cstart);
         return hzero<T, C>();
     } else if constexpr (FN == FN_ACKLEY) {
-        if (has) return ackley_sweep<T, C, kRemap>(pt.ack, pt.sc, a.n, i, cstart);
+        if (has) return ackley_sweep<T, C, kRemap, kSparse>(pt.ack, pt.sc, a.n, i, cstart);
         return hzero<T, C>();
     } else {
-        return fp_sweep<T, C, MB, kRemap>(a, smem_raw, L, pt.x, pt.t1, pt.t2, pt.res, i, cstart, has, reload);
+        return fp_sweep<T, C, MB, kRemap, kSparse>(a, smem_raw, L, pt.x, pt.t1, pt.t2, pt.res, i, cstart, has, reload);
     }
 }
 
@@ -781,7 +799,7 @@ __host__ __device__ inline size_t sym_hs_bytes(int n, int C)
     return align_up((size_t)sym_hs_elems(n, C) * sizeof(T), 16);
 }
 
-template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+template <typename T, typename IO, int C, int FN, bool HVP, int MB, bool kSparse = false>
 __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -829,7 +847,7 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
         }
         if (FN != FN_FP && !has) continue;
         const int cstart = cn * C;
-        const HD<T, C> f = row_chunk<T, C, FN, MB, true>(job, smem_raw, L, pt, i, cstart, has, it == 0);
+        const HD<T, C> f = row_chunk<T, C, FN, MB, true, kSparse>(job, smem_raw, L, pt, i, cstart, has, it == 0);
         if (!has) continue;
         if constexpr (HVP) {
             T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
@@ -917,11 +935,11 @@ size_t sym_smem_bytes(const SweepArgs &a)
     return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n, C) : 0);
 }
 
-template <typename T, typename IO, int C, int FN, bool HVP, int MB>
+template <typename T, typename IO, int C, int FN, bool HVP, int MB, bool kSparse = false>
 cudaError_t launch_sym(SweepArgs a, cudaStream_t stream)
 {
     const size_t bytes = sym_smem_bytes<T, IO, C, FN, HVP, MB>(a);
-    auto kern = sym_kernel<T, IO, C, FN, HVP, MB>;
+    auto kern = sym_kernel<T, IO, C, FN, HVP, MB, kSparse>;
     static int configured[64] = {0};
     cudaError_t e = opt_in_smem(kern, bytes, configured);
     if (e != cudaSuccess) return e;

@@ -65,8 +65,11 @@ def test_argument_errors_without_gpu():
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
     bad = cf.Config(5, 4, 256)
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
-    bad = cf.Config(4, 0, 0, 2, 0)  # unknown method
+    bad = cf.Config(4, 0, 0, 3, 0)  # unknown method
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
+    for c in (1, 2, 32):  # seed-sparse kernels: chunk sizes 4, 8 and 16 only
+        bad = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, 32)
+        assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
     for tpp in (16, 48, 512):
         bad = cf.Config(4, 0, 0, cf.SYMMETRIC, tpp)
         assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9

@@ -191,3 +191,61 @@ def test_symmetric_deterministic_and_equal_to_plain_within_bound():
     p = d.hvp(cfg=cf.Config(8, 1, 256))
     ref, hn = d.ref_hvp()
     assert np.max(np.linalg.norm(a - p, axis=1) / (hn * np.linalg.norm(d.vh, axis=1))) <= 2e-12
+
+
+# ------------------------------------------------------------------ seed-sparse symmetric method
+SPARSE_CHUNKS = [4, 8, 16]
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("c", SPARSE_CHUNKS)
+def test_symmetric_sparse_every_chunk(fn, prec, c):
+    """The seed-sparse symmetric kernels against the oracle: n = 19 and 37
+    (ragged last chunk; variables on both sides of the seeded chunk)."""
+    for n, seed in ((19, 500 + c), (37, 600 + c)):
+        d = Dev(W.make_batch(fn, n, 61, seed=seed), prec)
+        for tpp in (32, 64):
+            cfg = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, tpp)
+            e = hvp_err(d, d.hvp(cfg=cfg))
+            assert e.max() <= BOUND[prec], (n, tpp, e.max())
+            e = hessian_err(d, d.hessian(cfg=cfg))
+            assert e.max() <= BOUND[prec], (n, tpp, e.max())
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 64, 128])
+def test_symmetric_sparse_sizes(fn, prec, n):
+    batch = 40 if n <= 64 else 6
+    d = Dev(W.make_batch(fn, n, batch, seed=700 + n), prec)
+    for c in SPARSE_CHUNKS:
+        cfg = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, 0)
+        assert hvp_err(d, d.hvp(cfg=cfg)).max() <= BOUND[prec], c
+        assert hessian_err(d, d.hessian(cfg=cfg)).max() <= BOUND[prec], c
+
+
+def test_symmetric_sparse_matches_dense_and_is_deterministic():
+    for fn in FNS:
+        d = Dev(W.make_batch(fn, 48, 200, seed=9), cf.FP64)
+        sp = cf.Config(8, 0, 0, cf.SYMMETRIC_SPARSE, 32)
+        a = d.hvp(cfg=sp)
+        assert np.array_equal(a, d.hvp(cfg=sp))
+        dense = d.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC, 32))
+        ref, hn = d.ref_hvp()
+        assert np.max(np.linalg.norm(a - dense, axis=1) / (hn * np.linalg.norm(d.vh, axis=1))) <= 2e-12
+
+
+def test_symmetric_sparse_chunk_auto_and_nan_point():
+    """csize = 0 with the seed-sparse method picks one of its chunk sizes; a
+    NaN input reaches its own point's output and no other point's."""
+    b = W.make_batch(W.ROSENBROCK, 21, 30, seed=11)
+    b.x[4, 7] = np.nan
+    d = Dev(b, cf.FP64)
+    out = d.hvp(cfg=cf.Config(0, 0, 0, cf.SYMMETRIC_SPARSE, 32))
+    assert np.any(np.isnan(out[4]))
+    ok = np.ones(30, bool)
+    ok[4] = False
+    assert np.all(np.isfinite(out[ok]))
+    e = hvp_err(d, out)
+    assert e[ok].max() <= BOUND[cf.FP64]

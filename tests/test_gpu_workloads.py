@@ -97,3 +97,19 @@ def test_error_report_every_workload():
     if path:
         with open(path, "w") as f:
             json.dump(rows, f, indent=1)
+
+
+@pytest.mark.parametrize("prec", [cf.FP32_COMP, cf.FP64])
+def test_symmetric_sparse_full_workloads(prec):
+    """The seed-sparse symmetric method at the full sizes of every named
+    workload, in the configuration the benchmark reports for it."""
+    for name, c in (("rosenbrock_n16", 4), ("ackley_n64", 8), ("fletcher_powell_n32", 8), ("rosenbrock_n256", 16)):
+        d = Dev(W.workload(name), prec)
+        cfg = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, 32)
+        if name == "rosenbrock_n256" and prec == cf.FP64:
+            # FP64 symmetric HVP stages at most n ~ 200 in shared memory: Hessian
+            rows = slice(0, 128)
+            assert hessian_err(d, d.hessian(cfg=cfg), rows).max() <= BOUND[prec]
+            continue
+        e = hvp_err(d, d.hvp(cfg=cfg))
+        assert e.max() <= BOUND[prec], (name, e.max())
