@@ -66,6 +66,9 @@ class _FP(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("E", ctypes.c_void_p), ("ld", ctypes.c_int)]
 
 
+UNARY_OPS = ("sin", "cos", "exp", "sqrt", "log", "tanh", "tan", "recip", "abs")
+
+
 def _load():
     global _lib
     with _lock:
@@ -90,12 +93,14 @@ def _load():
             lib.orc_chess_vec_batch.argtypes = [I, I, I, L, P, P, P, P]
             lib.orc_chunk_init.argtypes = [I, P, P, I, I, I]
             lib.orc_chunk_init.restype = None
-            for name in ("orc_hd_mul", "orc_hd_add"):
+            for name in ("orc_hd_mul", "orc_hd_add", "orc_hd_div"):
                 getattr(lib, name).argtypes = [I, P, P, P]
                 getattr(lib, name).restype = None
-            for name in ("orc_hd_sin", "orc_hd_cos", "orc_hd_exp", "orc_hd_sqrt"):
-                getattr(lib, name).argtypes = [I, P, P]
-                getattr(lib, name).restype = None
+            for name in UNARY_OPS:
+                getattr(lib, f"orc_hd_{name}").argtypes = [I, P, P]
+                getattr(lib, f"orc_hd_{name}").restype = None
+            lib.orc_hd_pow.argtypes = [I, P, P, ctypes.c_double]
+            lib.orc_hd_pow.restype = None
             lib.orc_eval_hd.argtypes = [I, I, I, P, P, P]
             lib.orc_eval_hd.restype = None
             lib.orc_count_reset.restype = None
@@ -272,14 +277,19 @@ def eval_hd(fn: int, c: int, y, params: FPParams | None = None) -> np.ndarray:
 
 
 def hd_op(op: str, c: int, a, b=None) -> np.ndarray:
-    """One hDual<c> operation: 'mul', 'add' (binary) or 'sin', 'cos', 'exp', 'sqrt'."""
+    """One hDual<c> operation: 'mul', 'add', 'div' (binary, b an hDual),
+    'pow' (b the scalar exponent) or one of UNARY_OPS."""
     a = _f64(a)
     r = np.empty(2 * c + 2)
     lib = _load()
-    if op in ("mul", "add"):
+    if op in ("mul", "add", "div"):
         b = _f64(b)
         getattr(lib, f"orc_hd_{op}")(c, _ptr(r), _ptr(a), _ptr(b))
+    elif op == "pow":
+        lib.orc_hd_pow(c, _ptr(r), _ptr(a), float(b))
     else:
+        if op not in UNARY_OPS:
+            raise ValueError(op)
         getattr(lib, f"orc_hd_{op}")(c, _ptr(r), _ptr(a))
     return r
 

@@ -56,7 +56,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-enum { ORC_ROSENBROCK = 0, ORC_ACKLEY = 1, ORC_FLETCHER_POWELL = 2 };
+enum { ORC_ROSENBROCK = 0, ORC_ACKLEY = 1, ORC_FLETCHER_POWELL = 2, ORC_MIX = 3 };
 
 /* Fletcher-Powell parameters: A, B are row-major with leading dimension ld,
  * of which the leading n x n block is used; E has n entries. */
@@ -225,12 +225,98 @@ static void fp_h(int n, const double *x, const orc_fp *p, double *H)
     free(r);
 }
 
+/* Test function of the extended operator set.  Sec. IV lists division, abs
+ * and comparisons among the overloaded operators, but none of the paper's
+ * three test functions uses them; this function does (it is defined here,
+ * not in the paper):
+ *   f = sum_{k<n-1} [ (x_{k+1} - x_k)^2 / (1 + x_k^2) + |x_k| x_{k+1}
+ *                     + tanh(x_k x_{k+1}) ]
+ *     + sum_k [ log(1 + x_k^2) + 0.1 (2 + x_k^2)^{3/2} + tan(0.3 x_k) ]
+ *     + (x_0 > x_{n-1} ? x_0 x_{n-1} : -x_0^2)
+ * |x| is differentiated as sign(x) x with sign(0) = +1; the branch is taken
+ * on values, and each branch is differentiated as it stands. */
+static double mix_f(int n, const double *x)
+{
+    double f = 0.0;
+    for (int k = 0; k + 1 < n; ++k) {
+        double d = x[k + 1] - x[k];
+        f += d * d / (1.0 + x[k] * x[k]) + fabs(x[k]) * x[k + 1] + tanh(x[k] * x[k + 1]);
+    }
+    for (int k = 0; k < n; ++k)
+        f += log(1.0 + x[k] * x[k]) + 0.1 * pow(2.0 + x[k] * x[k], 1.5) + tan(0.3 * x[k]);
+    f += (x[0] > x[n - 1]) ? x[0] * x[n - 1] : -x[0] * x[0];
+    return f;
+}
+
+static double sign1(double a) { return a < 0.0 ? -1.0 : 1.0; }
+
+/* Gradient, term by term (d = x_{k+1} - x_k, q = 1 + x_k^2, t = tanh(x_k x_{k+1})):
+ *   d/dx_k     [d^2/q] = -2d/q - 2 x_k d^2/q^2,  d/dx_{k+1} [d^2/q] = 2d/q
+ *   d/dx_k     [|x_k| x_{k+1}] = sign(x_k) x_{k+1},  d/dx_{k+1} = |x_k|
+ *   d/dx_k     [tanh] = (1 - t^2) x_{k+1},  d/dx_{k+1} = (1 - t^2) x_k
+ *   d/dx [log(1+x^2)] = 2x/(1+x^2);  d/dx [0.1 s^{3/2}] = 0.3 x s^{1/2} (s = 2+x^2);
+ *   d/dx [tan(0.3x)] = 0.3 (1 + tan^2(0.3x)). */
+static void mix_g(int n, const double *x, double *g)
+{
+    for (int k = 0; k < n; ++k) {
+        double s = 2.0 + x[k] * x[k], tau = tan(0.3 * x[k]);
+        g[k] = 2.0 * x[k] / (1.0 + x[k] * x[k]) + 0.3 * x[k] * sqrt(s) + 0.3 * (1.0 + tau * tau);
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        double d = x[k + 1] - x[k], q = 1.0 + x[k] * x[k], t = tanh(x[k] * x[k + 1]);
+        g[k] += -2.0 * d / q - 2.0 * x[k] * d * d / (q * q) + sign1(x[k]) * x[k + 1] + (1.0 - t * t) * x[k + 1];
+        g[k + 1] += 2.0 * d / q + fabs(x[k]) + (1.0 - t * t) * x[k];
+    }
+    if (x[0] > x[n - 1]) {
+        g[0] += x[n - 1];
+        g[n - 1] += x[0];
+    } else {
+        g[0] += -2.0 * x[0];
+    }
+}
+
+/* Hessian, term by term (a = x_k, d, q, t as above, T'' = -2t(1 - t^2)):
+ *   [d^2/q]:  H_kk += 2/q + 8ad/q^2 - 2d^2/q^2 + 8a^2 d^2/q^3,
+ *             H_{k,k+1} += -2/q - 4ad/q^2,  H_{k+1,k+1} += 2/q
+ *   [|x_k| x_{k+1}]:  H_{k,k+1} += sign(x_k)
+ *   [tanh]:  H_kk += T'' x_{k+1}^2,  H_{k+1,k+1} += T'' x_k^2,
+ *            H_{k,k+1} += T'' x_k x_{k+1} + (1 - t^2)
+ *   per variable:  (2 - 2x^2)/(1+x^2)^2 + 0.3 s^{1/2} + 0.3 x^2 s^{-1/2}
+ *                  + 0.18 tau (1 + tau^2),  tau = tan(0.3x)
+ *   branch:  x_0 > x_{n-1}: H_{0,n-1} = H_{n-1,0} += 1;  else H_00 += -2. */
+static void mix_h(int n, const double *x, double *H)
+{
+    memset(H, 0, sizeof(double) * (size_t)n * (size_t)n);
+    for (int k = 0; k < n; ++k) {
+        double xx = x[k] * x[k], s = 2.0 + xx, tau = tan(0.3 * x[k]);
+        H[(size_t)k * n + k] = (2.0 - 2.0 * xx) / ((1.0 + xx) * (1.0 + xx)) + 0.3 * sqrt(s) + 0.3 * xx / sqrt(s) +
+                               0.18 * tau * (1.0 + tau * tau);
+    }
+    for (int k = 0; k + 1 < n; ++k) {
+        double a = x[k], b = x[k + 1], d = b - a, q = 1.0 + a * a, t = tanh(a * b);
+        double t2 = -2.0 * t * (1.0 - t * t);
+        H[(size_t)k * n + k] += 2.0 / q + 8.0 * a * d / (q * q) - 2.0 * d * d / (q * q) + 8.0 * a * a * d * d / (q * q * q) +
+                                t2 * b * b;
+        H[(size_t)(k + 1) * n + k + 1] += 2.0 / q + t2 * a * a;
+        double off = -2.0 / q - 4.0 * a * d / (q * q) + sign1(a) + t2 * a * b + (1.0 - t * t);
+        H[(size_t)k * n + k + 1] += off;
+        H[(size_t)(k + 1) * n + k] += off;
+    }
+    if (x[0] > x[n - 1]) {
+        H[n - 1] += 1.0;
+        H[(size_t)(n - 1) * n] += 1.0;
+    } else {
+        H[0] += -2.0;
+    }
+}
+
 double orc_value(int fn, int n, const double *x, const orc_fp *p)
 {
     switch (fn) {
     case ORC_ROSENBROCK: return rosen_f(n, x);
     case ORC_ACKLEY: return ackley_f(n, x);
     case ORC_FLETCHER_POWELL: return fp_f(n, x, p);
+    case ORC_MIX: return mix_f(n, x);
     }
     return NAN;
 }
@@ -241,6 +327,7 @@ int orc_gradient(int fn, int n, const double *x, const orc_fp *p, double *g)
     case ORC_ROSENBROCK: rosen_g(n, x, g); return 0;
     case ORC_ACKLEY: ackley_g(n, x, g); return 0;
     case ORC_FLETCHER_POWELL: fp_g(n, x, p, g); return 0;
+    case ORC_MIX: mix_g(n, x, g); return 0;
     }
     return -1;
 }
@@ -251,6 +338,7 @@ int orc_hessian(int fn, int n, const double *x, const orc_fp *p, double *H)
     case ORC_ROSENBROCK: rosen_h(n, x, H); return 0;
     case ORC_ACKLEY: ackley_h(n, x, H); return 0;
     case ORC_FLETCHER_POWELL: fp_h(n, x, p, H); return 0;
+    case ORC_MIX: mix_h(n, x, H); return 0;
     }
     return -1;
 }
@@ -420,6 +508,46 @@ static void hd_sqrt(int c, double *r, const double *a)
     hd_unary(c, r, a, s, 0.5 / s, -0.25 / (s * a[0]));
 }
 
+/* The extended operator set, each through the unary rule above:
+ *   log u:      phi' = 1/u,         phi'' = -1/u^2
+ *   tanh u:     phi' = 1 - t^2,     phi'' = -2t (1 - t^2),   t = tanh u
+ *   tan u:      phi' = 1 + t^2,     phi'' = 2t (1 + t^2),    t = tan u
+ *   u^p:        phi' = p u^{p-1},   phi'' = p (p-1) u^{p-2}
+ *   1/u:        phi' = -1/u^2,      phi'' = 2/u^3
+ *   u / w = u * (1/w) by the product rule;
+ *   |u| = sign(u0) u componentwise, sign(0) = +1. */
+static void hd_log(int c, double *r, const double *a) { hd_unary(c, r, a, log(a[0]), 1.0 / a[0], -1.0 / (a[0] * a[0])); }
+static void hd_tanh(int c, double *r, const double *a)
+{
+    double t = tanh(a[0]);
+    hd_unary(c, r, a, t, 1.0 - t * t, -2.0 * t * (1.0 - t * t));
+}
+static void hd_tan(int c, double *r, const double *a)
+{
+    double t = tan(a[0]);
+    hd_unary(c, r, a, t, 1.0 + t * t, 2.0 * t * (1.0 + t * t));
+}
+static void hd_pow(int c, double *r, const double *a, double p)
+{
+    hd_unary(c, r, a, pow(a[0], p), p * pow(a[0], p - 1.0), p * (p - 1.0) * pow(a[0], p - 2.0));
+}
+static void hd_recip(int c, double *r, const double *a)
+{
+    hd_unary(c, r, a, 1.0 / a[0], -1.0 / (a[0] * a[0]), 2.0 / (a[0] * a[0] * a[0]));
+}
+static void hd_div(int c, double *r, const double *a, const double *b)
+{
+    double *w = (double *)malloc(sizeof(double) * HK(c));
+    hd_recip(c, w, b);
+    hd_mul(c, r, a, w);
+    free(w);
+}
+static void hd_abs(int c, double *r, const double *a)
+{
+    double s = a[0] < 0.0 ? -1.0 : 1.0;
+    for (int t = 0; t < HK(c); ++t) r[t] = s * a[t];
+}
+
 static void hd_zero(int c, double *r) { memset(r, 0, sizeof(double) * HK(c)); }
 static void hd_copy(int c, double *r, const double *a) { memcpy(r, a, sizeof(double) * HK(c)); }
 
@@ -503,12 +631,61 @@ static void fp_hd(int c, int n, const double *y, const orc_fp *p, double *out)
     free(sy);
 }
 
+/* The extended-operator test function on hDuals, in the order of its
+ * definition above. */
+static void mix_hd(int c, int n, const double *y, double *out)
+{
+    int K = HK(c);
+    double *acc = (double *)calloc(8 * (size_t)K, sizeof(double));
+    double *t1 = acc + K, *t2 = t1 + K, *t3 = t2 + K, *t4 = t3 + K, *t5 = t4 + K, *t6 = t5 + K, *t7 = t6 + K;
+    for (int k = 0; k + 1 < n; ++k) {
+        const double *yk = y + (size_t)k * K, *yk1 = y + (size_t)(k + 1) * K;
+        hd_sub(c, t1, yk1, yk);         /* d = x_{k+1} - x_k */
+        hd_mul(c, t2, t1, t1);          /* d^2 */
+        hd_mul(c, t3, yk, yk);          /* 1 + x_k^2 */
+        hd_sadd(c, t3, 1.0, t3);
+        hd_div(c, t4, t2, t3);          /* d^2 / (1 + x_k^2) */
+        hd_add(c, t5, acc, t4);
+        hd_abs(c, t1, yk);              /* |x_k| x_{k+1} */
+        hd_mul(c, t2, t1, yk1);
+        hd_add(c, t6, t5, t2);
+        hd_mul(c, t1, yk, yk1);         /* tanh(x_k x_{k+1}) */
+        hd_tanh(c, t2, t1);
+        hd_add(c, acc, t6, t2);
+    }
+    for (int k = 0; k < n; ++k) {
+        const double *yk = y + (size_t)k * K;
+        hd_mul(c, t1, yk, yk);          /* log(1 + x_k^2) */
+        hd_sadd(c, t2, 1.0, t1);
+        hd_log(c, t3, t2);
+        hd_add(c, t4, acc, t3);
+        hd_sadd(c, t2, 2.0, t1);        /* 0.1 (2 + x_k^2)^{3/2} */
+        hd_pow(c, t3, t2, 1.5);
+        hd_smul(c, t5, 0.1, t3);
+        hd_add(c, t6, t4, t5);
+        hd_smul(c, t1, 0.3, yk);        /* tan(0.3 x_k) */
+        hd_tan(c, t2, t1);
+        hd_add(c, acc, t6, t2);
+    }
+    const double *y0 = y, *yl = y + (size_t)(n - 1) * K;
+    if (y0[0] > yl[0]) {                /* comparison on values */
+        hd_mul(c, t1, y0, yl);
+    } else {
+        hd_mul(c, t2, y0, y0);
+        hd_smul(c, t1, -1.0, t2);
+    }
+    hd_add(c, t7, acc, t1);
+    hd_copy(c, out, t7);
+    free(acc);
+}
+
 static void eval_hd(int fn, int c, int n, const double *y, const orc_fp *p, double *out)
 {
     switch (fn) {
     case ORC_ROSENBROCK: rosen_hd(c, n, y, out); break;
     case ORC_ACKLEY: ackley_hd(c, n, y, out); break;
     case ORC_FLETCHER_POWELL: fp_hd(c, n, y, p, out); break;
+    case ORC_MIX: mix_hd(c, n, y, out); break;
     }
 }
 
@@ -647,6 +824,13 @@ void orc_hd_sin(int c, double *r, const double *a) { hd_sin(c, r, a); }
 void orc_hd_cos(int c, double *r, const double *a) { hd_cos(c, r, a); }
 void orc_hd_exp(int c, double *r, const double *a) { hd_exp(c, r, a); }
 void orc_hd_sqrt(int c, double *r, const double *a) { hd_sqrt(c, r, a); }
+void orc_hd_log(int c, double *r, const double *a) { hd_log(c, r, a); }
+void orc_hd_tanh(int c, double *r, const double *a) { hd_tanh(c, r, a); }
+void orc_hd_tan(int c, double *r, const double *a) { hd_tan(c, r, a); }
+void orc_hd_recip(int c, double *r, const double *a) { hd_recip(c, r, a); }
+void orc_hd_abs(int c, double *r, const double *a) { hd_abs(c, r, a); }
+void orc_hd_pow(int c, double *r, const double *a, double p) { hd_pow(c, r, a, p); }
+void orc_hd_div(int c, double *r, const double *a, const double *b) { hd_div(c, r, a, b); }
 
 /* Evaluate f on a caller-seeded hDual array y (n hDuals of size 2c+2). */
 void orc_eval_hd(int fn, int c, int n, const double *y, const orc_fp *p, double *out)

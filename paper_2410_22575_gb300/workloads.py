@@ -30,8 +30,12 @@ from dataclasses import dataclass, field
 import numpy as np
 
 ROSENBROCK, ACKLEY, FLETCHER_POWELL = 0, 1, 2
-FN_NAMES = {ROSENBROCK: "rosenbrock", ACKLEY: "ackley", FLETCHER_POWELL: "fletcher_powell"}
-X_RANGE = {ROSENBROCK: (-2.0, 2.0), ACKLEY: (-5.0, 5.0), FLETCHER_POWELL: (-math.pi, math.pi)}
+# A test function of the extended operator set (division, abs, log, tanh,
+# tan, pow and a comparison), evaluated through the user-function interface;
+# the library has no built-in id for it.
+MIX = 3
+FN_NAMES = {ROSENBROCK: "rosenbrock", ACKLEY: "ackley", FLETCHER_POWELL: "fletcher_powell", MIX: "mix"}
+X_RANGE = {ROSENBROCK: (-2.0, 2.0), ACKLEY: (-5.0, 5.0), FLETCHER_POWELL: (-math.pi, math.pi), MIX: (-2.0, 2.0)}
 
 
 @dataclass

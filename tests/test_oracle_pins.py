@@ -15,7 +15,7 @@ import pytest
 
 from paper_2410_22575_gb300 import workloads as W
 
-R, A, F = W.ROSENBROCK, W.ACKLEY, W.FLETCHER_POWELL
+R, A, F, M = W.ROSENBROCK, W.ACKLEY, W.FLETCHER_POWELL, W.MIX
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
@@ -148,7 +148,7 @@ def _fd_hess(orc, fn, x, p, h):
     return H
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 @pytest.mark.parametrize("n", [1, 2, 3, 6])
 def test_gradient_vs_finite_differences(orc, fn, n):
     p = _params(orc, fn, n)
@@ -159,7 +159,7 @@ def test_gradient_vs_finite_differences(orc, fn, n):
         assert np.max(np.abs(g - gfd)) <= 1e-6 * max(1.0, np.max(np.abs(g)))
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 @pytest.mark.parametrize("n", [1, 2, 3, 6])
 def test_hessian_vs_finite_differences(orc, fn, n):
     p = _params(orc, fn, n)
@@ -170,7 +170,7 @@ def test_hessian_vs_finite_differences(orc, fn, n):
         assert np.max(np.abs(H - Hfd)) <= 1e-6 * max(1.0, np.max(np.abs(H)))
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 def test_hvp_vs_directional_difference(orc, fn):
     n = 5
     p = _params(orc, fn, n)
@@ -184,7 +184,7 @@ def test_hvp_vs_directional_difference(orc, fn):
         assert np.max(np.abs(r - d)) <= 1e-6 * max(1.0, np.max(np.abs(r)))
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 def test_hessian_symmetric(orc, fn):
     for n in (2, 7, 33):
         p = _params(orc, fn, n)
@@ -259,6 +259,75 @@ def test_unary_rules_against_calculus(orc):
         np.testing.assert_allclose(orc.hd_op(op, 1, u), want, rtol=1e-14, atol=1e-14)
 
 
+def test_extended_unary_rules_against_calculus(orc):
+    """log, tanh, tan, 1/u, u^p of g(x, y) = x*y: the mixed second derivative
+    is phi'(xy) + phi''(xy) x y, with phi', phi'' from calculus."""
+    x, y = 1.3, 0.8
+    u = orc.hd_op("mul", 1, [x, 1, 0, 0], [y, 0, 1, 0])
+    t = x * y
+    th, tn = math.tanh(t), math.tan(t)
+    cases = {
+        "log": (math.log(t), 1 / t, -1 / t ** 2),
+        "tanh": (th, 1 / math.cosh(t) ** 2, -2 * th / math.cosh(t) ** 2),
+        "tan": (tn, 1 / math.cos(t) ** 2, 2 * tn / math.cos(t) ** 2),
+        "recip": (1 / t, -1 / t ** 2, 2 / t ** 3),
+    }
+    for op, (f0, f1, f2) in cases.items():
+        want = [f0, f1 * y, f1 * x, f1 + f2 * x * y]
+        np.testing.assert_allclose(orc.hd_op(op, 1, u), want, rtol=1e-14, atol=1e-14)
+    for p in (1.5, -0.5, 3.0):
+        want = [t ** p, p * t ** (p - 1) * y, p * t ** (p - 1) * x, p * t ** (p - 1) + p * (p - 1) * t ** (p - 2) * x * y]
+        np.testing.assert_allclose(orc.hd_op("pow", 1, u, p), want, rtol=1e-14, atol=1e-14)
+
+
+def test_division_and_abs_rules(orc):
+    """x / y with x seeded as x_i, y as x_j: d/dx = 1/y, d/dy = -x/y^2,
+    d2/dxdy = -1/y^2 (quotient rule).  |x*y|: sign(xy) times every component,
+    sign(0) = +1."""
+    x, y = 1.7, -0.6
+    q = orc.hd_op("div", 1, [x, 1, 0, 0], [y, 0, 1, 0])
+    np.testing.assert_allclose(q, [x / y, 1 / y, -x / y ** 2, -1 / y ** 2], rtol=1e-15, atol=1e-15)
+    # x_i = x_j = x (one variable): d/dx (x / x^2) = -1/x^2, d2/dx2 = 2/x^3
+    xx = orc.hd_op("mul", 1, [x, 1, 1, 0], [x, 1, 1, 0])
+    q = orc.hd_op("div", 1, [x, 1, 1, 0], xx)
+    np.testing.assert_allclose(q, [1 / x, -1 / x ** 2, -1 / x ** 2, 2 / x ** 3], rtol=1e-14, atol=1e-14)
+    u = orc.hd_op("mul", 1, [x, 1, 0, 0], [y, 0, 1, 0])
+    np.testing.assert_array_equal(orc.hd_op("abs", 1, u), -u)
+    np.testing.assert_array_equal(orc.hd_op("abs", 1, -u), -u)
+    z = np.array([0.0, 2.0, -3.0, 4.0])
+    np.testing.assert_array_equal(orc.hd_op("abs", 1, z), z)
+
+
+def test_mix_hand_values(orc):
+    """The extended-operator function at hand-computed points.  n = 1:
+    f = log(1+x^2) + 0.1 (2+x^2)^{3/2} + tan(0.3x) - x^2 (the comparison
+    x_0 > x_0 is false).  n = 2 at x = (1, 0): d = -1, q = 2, the branch
+    takes x_0 x_1 (1 > 0)."""
+    for x0 in (0.0, 0.5, -1.2):
+        f = math.log(1 + x0 * x0) + 0.1 * (2 + x0 * x0) ** 1.5 + math.tan(0.3 * x0) - x0 * x0
+        assert abs(orc.value(M, np.array([x0])) - f) <= 1e-15 * max(1, abs(f))
+    x = np.array([1.0, 0.0])
+    f = 1 / 2 + 0 + 0 + (math.log(2) + 0.1 * 3 ** 1.5 + math.tan(0.3)) + (0.1 * 2 ** 1.5) + 0
+    assert abs(orc.value(M, x) - f) <= 1e-14
+    H = orc.hessian(M, x)
+    # H_01: -2/q - 4ad/q^2 + sign(1) + tanh'(0) + T''(0)*0 + branch 1 = -1 + 1 + 1 + 1 + 1
+    assert abs(H[0, 1] - 3.0) <= 1e-14 and H[1, 0] == H[0, 1]
+    # H_11: 2/q + T''(0) x_0^2 + log'' (2) + 0.3 sqrt(2) + 0 + 0
+    assert abs(H[1, 1] - (1.0 + 2.0 + 0.3 * math.sqrt(2))) <= 1e-14
+
+
+def test_mix_abs_sign_at_zero(orc):
+    """|x_k| x_{k+1} at x_k = 0 contributes sign(0) = +1 to H_{k,k+1} in both
+    implementations (the convention, not a derivative)."""
+    x = np.array([0.0, 0.7, -0.4])
+    H = orc.hessian(M, x)
+    for c in (1, 2, 3):
+        np.testing.assert_allclose(orc.chunk_hess(M, x, c), H, rtol=0, atol=1e-14)
+    x2 = x.copy()
+    x2[0] = -1e-300  # sign flips to -1
+    assert abs((orc.hessian(M, x) - orc.hessian(M, x2))[0, 1] - 2.0) <= 1e-12
+
+
 def test_chunk_init_seeding(orc):
     """Alg. 4: v[0] = a_k, v[1] = [k == i], v[k - cstart + 2] = 1 for k in the
     chunk, all else 0 -- including the case where row i lies in the chunk."""
@@ -279,7 +348,7 @@ def test_chunk_init_seeding(orc):
 
 
 # ------------------------------------------------------------------ O1 == O2
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 @pytest.mark.parametrize("n", [1, 2, 5, 16, 33])
 def test_chunk_hess_equals_closed_form(orc, fn, n):
     p = _params(orc, fn, n)
@@ -291,7 +360,7 @@ def test_chunk_hess_equals_closed_form(orc, fn, n):
         assert np.linalg.norm(Hc - H) <= 1e-13 * scale, (c, np.linalg.norm(Hc - H) / scale)
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 @pytest.mark.parametrize("n", [3, 10])
 def test_schunk_hess_equals_chunk_hess(orc, fn, n):
     p = _params(orc, fn, n)
@@ -302,7 +371,7 @@ def test_schunk_hess_equals_chunk_hess(orc, fn, n):
         assert np.linalg.norm(H1 - H2) <= 1e-13 * np.linalg.norm(H1)
 
 
-@pytest.mark.parametrize("fn", [R, A, F])
+@pytest.mark.parametrize("fn", [R, A, F, M])
 @pytest.mark.parametrize("n", [1, 4, 11])
 def test_chess_vec_and_sc_hess_vec(orc, fn, n):
     p = _params(orc, fn, n)
