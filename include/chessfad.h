@@ -84,6 +84,7 @@ typedef struct CUstream_st *chessfad_stream_t;
 #define CHESSFAD_ERR_CONFIG (-9)    /* launch configuration out of range */
 #define CHESSFAD_ERR_CUDA (-10)     /* CUDA runtime / launch error */
 #define CHESSFAD_ERR_PLAN (-11)     /* ragged plan invalid or built for another precision */
+#define CHESSFAD_ERR_JIT (-12)      /* user function: NVRTC unavailable or the source did not compile */
 
 /* Fletcher-Powell parameters, shared by the whole batch.  A, B: device,
  * double, row-major with leading dimension ld >= n; the leading n x n block
@@ -275,6 +276,69 @@ CHESSFAD_API const char *chessfad_strerror(int status);
 
 /* Library version, major*10000 + minor*100 + patch. */
 CHESSFAD_API int chessfad_version(void);
+
+/* ---------------------------------------------------------------------------
+ * User-supplied functions.
+ *
+ * The paper's premise (Sec. I, Sec. IV) is that the user writes f once,
+ * generically, and instantiates it on hDual numbers; a compiled library
+ * cannot instantiate the caller's template, so here the caller passes the
+ * source text of f and the library compiles it at run time (NVRTC, sm_103a)
+ * together with its hDual operators and the CHESS-VEC (Alg. 7) /
+ * CHUNK-HESS (Alg. 5) sweep, once per handle.  The source must define
+ *
+ *     template <class R, class X>
+ *     R NAME(const X &x, int n, const double *params)
+ *
+ * (device code; __device__ may be omitted).  x[k], 0 <= k < n, is variable k
+ * as an R; R supports + - * / with R and with double on either side, unary
+ * -, += -= *= /=, the comparisons < <= > >= == != (on values, also against
+ * double), value(u), and the functions sin cos tan tanh exp log sqrt
+ * pow(u, double) abs fabs fmin fmax; a double converts to an R constant.
+ * Division, abs and comparisons are among the overloads Sec. IV lists; their
+ * rules are the quotient rule (u / w = u * (1/w)), sign(u) u with sign(0) =
+ * +1, and a comparison of values (the branch taken is differentiated as it
+ * stands).  params is the caller's device pointer, passed through (may be
+ * NULL).  The arithmetic of f runs in the handle's precision: FP64, or FP32
+ * (CHESSFAD_FP32_COMP: only the row-times-v reduction is compensated; the
+ * function's own sums are plain FP32 as written).
+ *
+ * The decomposition is one thread per (point, Hessian row), sweeping the row's
+ * ceil(n/csize) chunks; x, v, out, H as for chessfad_hvp / chessfad_hessian,
+ * 1 <= n <= CHESSFAD_MAX_N.
+ * --------------------------------------------------------------------------- */
+typedef struct chessfad_user_fn chessfad_user_fn;
+
+/* Compile `source` for chunk size csize (1, 2, 4, 8, 16 or 32) and precision
+ * prec, and load it on the current device.  name: the function template's
+ * name (a C identifier).  *fn receives the handle (NULL on failure).  log
+ * (may be NULL) receives NVRTC's messages, NUL-terminated, truncated to
+ * log_bytes.  Returns CHESSFAD_ERR_JIT if NVRTC is missing or compilation
+ * fails, CHESSFAD_ERR_CUDA if the compiled code cannot be loaded (no
+ * device); synchronous; allocates host memory and the loaded module only. */
+CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, int csize, int prec,
+                                         chessfad_user_fn **fn, char *log, size_t log_bytes);
+
+/* Unload and free a handle (NULL is a no-op).  No launch using it may still
+ * be in flight. */
+CHESSFAD_API int chessfad_user_fn_destroy(chessfad_user_fn *fn);
+
+/* The handle's chunk size and precision, and the registers per thread and
+ * local (spill/stack) bytes of its HVP (hvp != 0) or Hessian kernel.  Any
+ * output pointer may be NULL. */
+CHESSFAD_API int chessfad_user_fn_info(const chessfad_user_fn *fn, int hvp, int *csize, int *prec, int *registers,
+                                       int *local_bytes);
+
+/* out[p] = H(x_p) v_p for the user's f (CHESS-VEC, Alg. 7), p < batch; types
+ * by the handle's precision (double, or float for CHESSFAD_FP32_COMP).
+ * Asynchronous on `stream`; allocates nothing. */
+CHESSFAD_API int chessfad_user_hvp(const chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
+                                   void *out, const double *params, chessfad_stream_t stream);
+
+/* H[p] = the Hessian of the user's f at x_p, every entry (CHUNK-HESS,
+ * Alg. 5), [batch][n][n]. */
+CHESSFAD_API int chessfad_user_hessian(const chessfad_user_fn *fn, int n, long long batch, const void *x, void *H,
+                                       const double *params, chessfad_stream_t stream);
 
 #ifdef __cplusplus
 }

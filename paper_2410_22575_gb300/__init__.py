@@ -90,6 +90,16 @@ def load(build_if_missing: bool = True):
         lib.chessfad_hvp_ragged.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
         lib.chessfad_hvp_ragged_noalloc.argtypes = [P, P, P, P, P, P]
         lib.chessfad_hvp_ragged_noalloc.restype = I
+        lib.chessfad_user_fn_create.argtypes = [ctypes.c_char_p, ctypes.c_char_p, I, I, ctypes.POINTER(P),
+                                                ctypes.c_char_p, ctypes.c_size_t]
+        lib.chessfad_user_fn_destroy.argtypes = [P]
+        lib.chessfad_user_fn_info.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                              ctypes.POINTER(I)]
+        lib.chessfad_user_hvp.argtypes = [P, I, L, P, P, P, P, P]
+        lib.chessfad_user_hessian.argtypes = [P, I, L, P, P, P, P]
+        for name in ("chessfad_user_fn_create", "chessfad_user_fn_destroy", "chessfad_user_fn_info",
+                     "chessfad_user_hvp", "chessfad_user_hessian"):
+            getattr(lib, name).restype = I
         lib.chessfad_strerror.argtypes = [I]
         lib.chessfad_strerror.restype = ctypes.c_char_p
         lib.chessfad_version.argtypes = []
@@ -322,6 +332,82 @@ class RaggedPlan:
     def close(self):
         if self.handle:
             chessfad_ragged_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ user-supplied functions
+def chessfad_user_fn_create(source: str, name: str, csize: int, prec: int, log_bytes: int = 16384):
+    """Compile a user function (see include/chessfad.h).  Returns
+    (status, handle or None, NVRTC log)."""
+    h = ctypes.c_void_p()
+    log = ctypes.create_string_buffer(log_bytes)
+    st = load().chessfad_user_fn_create(source.encode(), name.encode(), csize, prec, ctypes.byref(h), log,
+                                        log_bytes)
+    return st, (h.value if st == SUCCESS else None), log.value.decode(errors="replace")
+
+
+def chessfad_user_fn_destroy(handle) -> int:
+    return load().chessfad_user_fn_destroy(handle)
+
+
+def chessfad_user_fn_info(handle, hvp=True) -> dict:
+    c, p, r, lb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().chessfad_user_fn_info(handle, int(bool(hvp)), ctypes.byref(c), ctypes.byref(p), ctypes.byref(r),
+                                        ctypes.byref(lb)), "chessfad_user_fn_info")
+    return {"csize": c.value, "prec": p.value, "registers": r.value, "local_bytes": lb.value}
+
+
+def chessfad_user_hvp(handle, n, batch, x, v, out, params=None, stream=None) -> int:
+    return load().chessfad_user_hvp(handle, n, batch, _addr(x), _addr(v), _addr(out), _addr(params),
+                                    _stream(stream))
+
+
+def chessfad_user_hessian(handle, n, batch, x, H, params=None, stream=None) -> int:
+    return load().chessfad_user_hessian(handle, n, batch, _addr(x), _addr(H), _addr(params), _stream(stream))
+
+
+class UserFunction:
+    """A user-supplied f compiled for one chunk size and precision.  ``source``
+    defines ``template <class R, class X> R name(const X &x, int n, const
+    double *params)``; params (optional) is a float64 device tensor passed
+    through to f."""
+
+    def __init__(self, source: str, name: str, csize: int = 8, prec: int = FP64):
+        st, self.handle, self.log = chessfad_user_fn_create(source, name, csize, prec)
+        if st != SUCCESS:
+            raise ChessfadError(st, f"chessfad_user_fn_create: {self.log.strip()}")
+        self.csize, self.prec, self.name = csize, prec, name
+
+    def info(self, hvp=True) -> dict:
+        return chessfad_user_fn_info(self.handle, hvp)
+
+    def hvp(self, x, v, params=None, stream=None, out=None):
+        import torch
+
+        batch, n = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        _check(chessfad_user_hvp(self.handle, n, batch, x, v, out, params, stream), "chessfad_user_hvp")
+        return out
+
+    def hessian(self, x, params=None, stream=None, out=None):
+        import torch
+
+        batch, n = x.shape
+        if out is None:
+            out = torch.empty((batch, n, n), dtype=x.dtype, device=x.device)
+        _check(chessfad_user_hessian(self.handle, n, batch, x, out, params, stream), "chessfad_user_hessian")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            chessfad_user_fn_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

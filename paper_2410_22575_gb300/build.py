@@ -48,9 +48,32 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+# Sources compiled at run time (NVRTC) for user-supplied functions, embedded
+# in the library as string constants: (C++ name, file under csrc/).
+EMBEDDED = (("kHdualSrc", "hdual.cuh"), ("kUserNumSrc", "user_num.cuh"), ("kUserKernelSrc", "user_kernel.cuh"))
+DELIM = "CHESSFAD_EMBED"
+
+
+def write_embedded() -> str:
+    """Write _build/user_embed.h: each run-time-compiled source as a raw string."""
+    lines = ["// Generated by build.py from csrc/: sources compiled at run time by NVRTC.", "#pragma once"]
+    for cname, fname in EMBEDDED:
+        text = open(os.path.join(CSRC, fname)).read()
+        if f"){DELIM}" in text:
+            raise RuntimeError(f"{fname} contains the raw-string delimiter")
+        lines.append(f'static const char {cname}[] = R"{DELIM}({text}){DELIM}";')
+    path = os.path.join(OUT, "user_embed.h")
+    body = "\n".join(lines) + "\n"
+    if not os.path.exists(path) or open(path).read() != body:
+        with open(path, "w") as f:
+            f.write(body)
+    return path
+
+
 def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
     obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + (["-Xptxas", "-v"] if verbose_ptxas else []) + ["-c", src, "-o", obj]
+    cmd = ([nvcc()] + ARCH + FLAGS + ["-I", OUT] + (["-Xptxas", "-v"] if verbose_ptxas else [])
+           + ["-c", src, "-o", obj])
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{p.stdout}\n{p.stderr}")
@@ -61,6 +84,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if not force and up_to_date():
         return LIB
     os.makedirs(OUT, exist_ok=True)
+    write_embedded()
     srcs = sources()
     jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
     logs = []
@@ -68,7 +92,7 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         for obj, log in ex.map(lambda s: _compile(s, verbose_ptxas), srcs):
             logs.append((obj, log))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in logs] + ["-cudart", "static"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in logs] + ["-cudart", "static", "-ldl"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stdout}\n{p.stderr}")

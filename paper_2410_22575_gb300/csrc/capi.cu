@@ -406,6 +406,7 @@ const char *chessfad_strerror(int status)
     case CHESSFAD_ERR_CONFIG: return "launch configuration out of range";
     case CHESSFAD_ERR_CUDA: return "CUDA runtime or launch error";
     case CHESSFAD_ERR_PLAN: return "ragged plan invalid or built for another precision";
+    case CHESSFAD_ERR_JIT: return "user function: NVRTC unavailable or compilation failed";
     }
     return "unknown status";
 }

@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol():
 def test_version_and_strerror():
     assert cf.chessfad_version() >= 100
     assert cf.strerror(0) == "success"
-    for code in range(-11, 0):
+    for code in range(-12, 0):
         assert cf.strerror(code) != "unknown status"
     assert cf.strerror(-99) == "unknown status"
 
