@@ -55,12 +55,15 @@ def sym_items(n: int, c: int) -> int:
 
 def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
     """Model flops of one Ackley HVP by the dense chunked-hDual method (the
-    Sec. V operation model extended to Ackley's op list; FMA = 2): per
-    evaluation of f, n(20c+12) + 22c+18; n*nch evaluations (plain, Alg. 7) or
-    sym_items(n, c) (symmetric, Alg. 8); plus 2n^2 for the row dots."""
+    Sec. V operation model extended to Ackley's op list as the kernel states
+    it; FMA = 2): per evaluation of f, n(14c+10) + 22c+18 -- per variable the
+    square y_k^2 by the unary rule accumulated into S (6c+4) and 2 pi y_k,
+    its cosine and the accumulation into Cs (8c+6); n*nch evaluations (plain,
+    Alg. 7) or sym_items(n, c) (symmetric, Alg. 8); plus 2n^2 for the row
+    dots."""
     nch = -(-n // c)
     sweeps = sym_items(n, c) if symmetric else n * nch
-    return sweeps * (n * (20 * c + 12) + 22 * c + 18) + 2 * n * n
+    return sweeps * (n * (14 * c + 10) + 22 * c + 18) + 2 * n * n
 
 
 # Sources that define the headline sweep kernel (the ncu traffic figure is
@@ -372,11 +375,11 @@ def gpu_arm(args):
 def model_flops_request(fn: int, n: int, c: int) -> float:
     """Model flops of one HVP by the dense chunked-hDual method (FMA = 2)."""
     nch = -(-n // c)
-    if fn == 0:
-        return n * nch * max(0, n - 1) * (38 * c + 21) + 2 * n * n
+    if fn == 0:  # per term three unary-rule accumulations (x_k^2, 100 d^2, (1-x_k)^2)
+        return n * nch * max(0, n - 1) * (18 * c + 12) + 2 * n * n
     if fn == 1:
         return model_flops_ackley(n, c)
-    return n * nch * (8 * n * n * (c + 1) + n * (20 * c + 11)) + 2 * n * n
+    return n * nch * (8 * n * n * (c + 1) + n * (14 * c + 9)) + 2 * n * n
 
 
 def ragged_arm(args, world, dev, stream, flush):
