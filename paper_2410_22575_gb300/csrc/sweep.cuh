@@ -553,6 +553,41 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
 // tile loads are block-wide: every thread of the block makes the same calls
 // (threads without a sweep pass has = false); with a single tile the load
 // happens only when `reload` is set.
+// MB consecutive shared-memory values starting at an element offset that is
+// a multiple of MB from a 16-byte-aligned base (the A/B tile rows), read with
+// the widest vector loads that alignment allows.
+template <typename T, int MB>
+__device__ __forceinline__ void load_rows(const T *__restrict__ p, T (&r)[MB])
+{
+    if constexpr (sizeof(T) == 4 && MB % 4 == 0) {
+#pragma unroll
+        for (int u = 0; u < MB; u += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(p + u);
+            r[u] = q.x;
+            r[u + 1] = q.y;
+            r[u + 2] = q.z;
+            r[u + 3] = q.w;
+        }
+    } else if constexpr (sizeof(T) == 4 && MB % 2 == 0) {
+#pragma unroll
+        for (int u = 0; u < MB; u += 2) {
+            const float2 q = *reinterpret_cast<const float2 *>(p + u);
+            r[u] = q.x;
+            r[u + 1] = q.y;
+        }
+    } else if constexpr (sizeof(T) == 8 && MB % 2 == 0) {
+#pragma unroll
+        for (int u = 0; u < MB; u += 2) {
+            const double2 q = *reinterpret_cast<const double2 *>(p + u);
+            r[u] = q.x;
+            r[u + 1] = q.y;
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < MB; ++u) r[u] = p[u];
+    }
+}
+
 template <typename T, int C, int MB, bool kRemap, bool kSparse>
 __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_raw, const Smem<T> &L, const T *xq,
                                              const T *ts, const T *tc, const T *res, int i, int cstart, bool has,
@@ -592,8 +627,9 @@ __device__ __forceinline__ HD<T, C> fp_sweep(const Job &a, unsigned char *smem_r
             for (int u = 0; u < MB; ++u) s[u] = hzero<T, C>();
             for_each_seed<T, C, 16, kRemap, kSparse>(xq, n, i, cstart, [&](int jv, const HD<T, C> &y) {
                 const T sj = ts[jv], cj = tc[jv];
-                const T *ar = At + jv * mt + (mb - m0);
-                const T *br = Bt + jv * mt + (mb - m0);
+                T ar[MB], br[MB];
+                load_rows<T, MB>(At + jv * mt + (mb - m0), ar);
+                load_rows<T, MB>(Bt + jv * mt + (mb - m0), br);
                 // sin(y_j) and cos(y_j) once per j (unary rule), then
                 // s_m += A_mj sin(y_j) + B_mj cos(y_j) for the MB rows.
                 const HD<T, C> sy = unary(y, sj, cj, -sj);
