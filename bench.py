@@ -53,17 +53,33 @@ def sym_items(n: int, c: int) -> int:
     return sum(min(c, n - R * c) * (nch - R) for R in range(nch))
 
 
-def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
-    """Model flops of one Ackley HVP by the dense chunked-hDual method (the
-    Sec. V operation model extended to Ackley's op list as the kernel states
-    it; FMA = 2): per evaluation of f, n(14c+10) + 22c+18 -- per variable the
-    square y_k^2 by the unary rule accumulated into S (6c+4) and 2 pi y_k,
-    its cosine and the accumulation into Cs (8c+6); n*nch evaluations (plain,
-    Alg. 7) or sym_items(n, c) (symmetric, Alg. 8); plus 2n^2 for the row
-    dots."""
+def model_flops_eval(fn: int, n: int, c: int) -> float:
+    """Model flops of one evaluation of f on hDual<c> (the Sec. V operation
+    model extended to each function's op list as the kernels state it; FMA =
+    2; a fused unary-rule accumulation acc += phi(u) counts 6c+4):
+    Rosenbrock (n-1)(18c+12) -- per term x_k^2, 100 d^2 and (1-x_k)^2;
+    Ackley n(14c+10) + 22c+18 -- per variable y_k^2 into S (6c+4) and
+    2 pi y_k, its cosine and the accumulation into Cs (8c+6), then the tail;
+    Fletcher-Powell 8n^2(c+1) + n(14c+9) -- per (m, j) two scalar-times-hDual
+    accumulations, per j sin and cos, per m the square of the residual."""
+    if fn == 0:
+        return max(0, n - 1) * (18 * c + 12)
+    if fn == 1:
+        return n * (14 * c + 10) + 22 * c + 18
+    return 8 * n * n * (c + 1) + n * (14 * c + 9)
+
+
+def model_flops_hvp(fn: int, n: int, c: int, symmetric: bool = False) -> float:
+    """Model flops of one HVP by the dense chunked-hDual method: n*nch
+    evaluations (plain, Alg. 7) or sym_items(n, c) (symmetric, Alg. 8), plus
+    2n^2 for the row dots."""
     nch = -(-n // c)
     sweeps = sym_items(n, c) if symmetric else n * nch
-    return sweeps * (n * (14 * c + 10) + 22 * c + 18) + 2 * n * n
+    return sweeps * model_flops_eval(fn, n, c) + 2 * n * n
+
+
+def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
+    return model_flops_hvp(1, n, c, symmetric)
 
 
 # Sources that define the headline sweep kernel (the ncu traffic figure is
@@ -276,12 +292,12 @@ def gpu_arm(args):
     od = torch.empty_like(xh, device=dev)
 
     def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        vd.copy_(vh, non_blocking=True)
-        st = cf.chessfad_hvp(fn, n, batch, 0, xd, vd, od, None, cf.FP32_COMP, stream)
+        # one C-ABI call: pinned host x, v -> device -> sweeps -> host out,
+        # copies of consecutive slices overlapping the sweeps
+        st = cf.chessfad_hvp_host(fn, n, batch, 0, xh, vh, oh, xd, vd, od, None, cf.FP32_COMP, args.e2e_slices,
+                                  stream)
         if st != 0:
-            raise cf.ChessfadError(st, "chessfad_hvp")
-        oh.copy_(od, non_blocking=True)
+            raise cf.ChessfadError(st, "chessfad_hvp_host")
 
     barrier(world)
     ms_e2e = timed_steps(e2e_step, args.steps, args.warmup, stream, flush)
@@ -358,7 +374,8 @@ def gpu_arm(args):
                      "frac_of_microbench": None if micro32 is None else achieved / micro32,
                      "fp64_peak_microbench": None if micro64 is None else micro64 / 1e12},
         "e2e": {"value": world * batch * args.steps / (tot_e2e * 1e-3), "unit": "HVP/s",
-                "h2d_bytes_per_step": 2 * batch * n * 4, "d2h_bytes_per_step": batch * n * 4},
+                "h2d_bytes_per_step": 2 * batch * n * 4, "d2h_bytes_per_step": batch * n * 4,
+                "api": "chessfad_hvp_host (pinned host buffers)", "slices": args.e2e_slices},
         "gpu_launches": f32["steps"],
         "clocks": f32.get("clocks"),
     }
@@ -373,13 +390,8 @@ def gpu_arm(args):
 
 # ------------------------------------------------------------------ uneven batch
 def model_flops_request(fn: int, n: int, c: int) -> float:
-    """Model flops of one HVP by the dense chunked-hDual method (FMA = 2)."""
-    nch = -(-n // c)
-    if fn == 0:  # per term three unary-rule accumulations (x_k^2, 100 d^2, (1-x_k)^2)
-        return n * nch * max(0, n - 1) * (18 * c + 12) + 2 * n * n
-    if fn == 1:
-        return model_flops_ackley(n, c)
-    return n * nch * (8 * n * n * (c + 1) + n * (14 * c + 9)) + 2 * n * n
+    """Model flops of one HVP of the uneven batch (plain method)."""
+    return model_flops_hvp(fn, n, c)
 
 
 def ragged_arm(args, world, dev, stream, flush):
@@ -604,6 +616,10 @@ def report(args):
             t = timed(lambda: cf.chessfad_hvp(b.fn, b.n, b.batch, 0, x, v, out, params, prec), reps)
             row = {"workload": name, "precision": "fp64" if prec == cf.FP64 else "fp32_comp",
                    "tuned": cfg.as_dict(), "hvp_per_s": b.batch / (t * 1e-3), "ms": t}
+            mf = model_flops_hvp(b.fn, b.n, cfg.csize, cfg.method == cf.SYMMETRIC)
+            peak = SM_COUNT * (FP64_LANES_PER_SM if prec == cf.FP64 else FP32_LANES_PER_SM) * 2 * SM_MAX_MHZ * 1e6
+            row["model_tflops"] = mf * b.batch / (t * 1e-3) / 1e12
+            row["frac_of_derived_peak"] = mf * b.batch / (t * 1e-3) / peak
             c0 = 4 if name == "rosenbrock_n16" else cfg.csize
             plain = cf.Config(c0, 1, 256)
             t = timed(lambda: cf.chessfad_hvp_config(b.fn, b.n, b.batch, plain, x, v, out, params, prec), reps)
@@ -728,6 +744,8 @@ def main():
     ap.add_argument("--csize", type=int, default=32)
     ap.add_argument("--tpr", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--e2e-slices", type=int, default=16,
+                    help="slices of the end-to-end call (copies of one overlap the sweep of the next)")
     ap.add_argument("--method", choices=["plain", "symmetric", "symmetric_sparse"], default="plain")
     ap.add_argument("--tpp", type=int, default=64, help="kernel-only, symmetric: threads per point")
     args = ap.parse_args()

@@ -166,6 +166,29 @@ CHESSFAD_API int chessfad_hvp_config(int fn, int n, long long batch, const chess
 CHESSFAD_API int chessfad_hessian_config(int fn, int n, long long batch, const chessfad_config *cfg, const void *x,
                             void *H, const chessfad_fp_params *params, int prec, chessfad_stream_t stream);
 
+/* chessfad_hvp for x, v and out in HOST memory, end to end: the batch is cut
+ * into `slices` contiguous parts (0 = 8; at most 64; at most batch); part k's
+ * x and v are copied host -> device, its HVPs computed (as chessfad_hvp with
+ * csize) and its out copied device -> host, with part k's sweep overlapping
+ * the copies of its neighbours (internal copy and compute streams of the
+ * current device, created on first use and kept until exit, joined to
+ * `stream` by events: the call is one stream-ordered operation on `stream`
+ * and can be captured into a CUDA graph from it).  Points are independent
+ * (Sec. VI, L0), so slicing changes no result beyond the launch
+ * configuration chessfad_hvp picks for the part's size.
+ *   x_host, v_host  host, [batch][n], double or float by prec; page-locked
+ *                   memory lets the copies overlap (pageable memory works
+ *                   but serialises them)
+ *   out_host        host, [batch][n]; valid once `stream` reaches this point
+ *   x_dev, v_dev, out_dev  device buffers of the whole batch (caller-owned
+ *                   staging; their contents are overwritten)
+ * Other arguments and errors as chessfad_hvp; slices out of range is
+ * CHESSFAD_ERR_CONFIG.  Concurrent calls for one device are serialised on a
+ * per-device lock while they enqueue.  Allocates no device memory. */
+CHESSFAD_API int chessfad_hvp_host(int fn, int n, long long batch, int csize, const void *x_host,
+                                   const void *v_host, void *out_host, void *x_dev, void *v_dev, void *out_dev,
+                                   const chessfad_fp_params *params, int prec, int slices, chessfad_stream_t stream);
+
 /* The configuration chessfad_hvp would use for csize = 0 (tuned entry if
  * present, else the default).  Host only; launches nothing. */
 CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg);

@@ -100,6 +100,8 @@ def load(build_if_missing: bool = True):
         for name in ("chessfad_user_fn_create", "chessfad_user_fn_destroy", "chessfad_user_fn_info",
                      "chessfad_user_hvp", "chessfad_user_hessian"):
             getattr(lib, name).restype = I
+        lib.chessfad_hvp_host.argtypes = [I, I, L, I, P, P, P, P, P, P, P, I, I, P]
+        lib.chessfad_hvp_host.restype = I
         lib.chessfad_strerror.argtypes = [I]
         lib.chessfad_strerror.restype = ctypes.c_char_p
         lib.chessfad_version.argtypes = []
@@ -152,6 +154,16 @@ def strerror(status: int) -> str:
 def chessfad_hvp(fn, n, batch, csize, x, v, out, params=None, prec=FP64, stream=None) -> int:
     p = ctypes.byref(params) if params is not None else None
     return load().chessfad_hvp(fn, n, batch, csize, _addr(x), _addr(v), _addr(out), p, prec, _stream(stream))
+
+
+def chessfad_hvp_host(fn, n, batch, csize, x_host, v_host, out_host, x_dev, v_dev, out_dev, params=None,
+                      prec=FP64, slices=0, stream=None) -> int:
+    """chessfad_hvp with host-resident x, v, out (tensors in host memory, or
+    addresses) and caller-owned device staging buffers; copies and sweeps of
+    consecutive slices overlap."""
+    p = ctypes.byref(params) if params is not None else None
+    return load().chessfad_hvp_host(fn, n, batch, csize, _addr(x_host), _addr(v_host), _addr(out_host),
+                                    _addr(x_dev), _addr(v_dev), _addr(out_dev), p, prec, slices, _stream(stream))
 
 
 def chessfad_hessian(fn, n, batch, csize, x, H, params=None, prec=FP64, stream=None) -> int:

@@ -75,6 +75,21 @@ def test_argument_errors_without_gpu():
         assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
 
 
+def test_host_pipeline_argument_errors_without_gpu():
+    lib = cf.load()
+    d = ctypes.c_void_p(16)
+    args = [d] * 6
+    assert lib.chessfad_hvp_host(3, 8, 4, 4, *args, None, 0, 0, None) == -1
+    assert lib.chessfad_hvp_host(0, 8, -1, 4, *args, None, 0, 0, None) == -3
+    assert lib.chessfad_hvp_host(0, 8, 4, 3, *args, None, 0, 0, None) == -4
+    assert lib.chessfad_hvp_host(0, 8, 4, 4, *args, None, 0, 65, None) == -9
+    assert lib.chessfad_hvp_host(0, 8, 4, 4, *args, None, 0, -1, None) == -9
+    assert lib.chessfad_hvp_host(0, 8, 4, 4, None, d, d, d, d, d, None, 0, 0, None) == -5
+    assert lib.chessfad_hvp_host(0, 8, 4, 4, d, d, d, d, d, None, None, 0, 0, None) == -5
+    assert lib.chessfad_hvp_host(2, 8, 4, 4, *args, None, 0, 0, None) == -6
+    assert lib.chessfad_hvp_host(0, 8, 0, 4, None, None, None, None, None, None, None, 0, 0, None) == 0
+
+
 @pytest.mark.parametrize("fn", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_default_config_host_only(fn, prec):
