@@ -319,11 +319,12 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
                                                  int i, int cstart)
 {
     const T z = opaque_zero<T>();
-    HD<T, C> S = hzero<T, C>();
+    HD<T, C> Sh = hzero<T, C>();  // S / 2: derivative components of sum y_k^2 / 2
     HD<T, C> Cs = hzero<T, C>();
-    // cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
+    // y^2 / 2 by the unary rule (phi' = y, phi'' = 1), doubled once after the
+    // sweep (exact); cos(2 pi t): phi' = -2 pi sin(2 pi t), phi'' = -4 pi^2 cos(2 pi t)
     auto term = [&](const AckEnt<T> &e, const HD<T, C> &y) {
-        add_unary<false>(S, y, T(0), T(2) * y.v, T(2));  // S += y^2 (unary rule of the square)
+        add_unary<false>(Sh, y, T(0), y.v, T(1));
         add_unary<false>(Cs, y, T(0), e.d1, e.d2);
     };
     const int lo = min(cstart, n), hi = min(cstart + C, n);
@@ -368,6 +369,7 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
             term(e, seed<T, C>(e.x, k, i, cstart, z));
         }
     }
+    HD<T, C> S = smul(T(2), Sh);
     S.v = sc[0];   // sum x_k^2        (FP64 island)
     Cs.v = sc[1];  // sum cos(2 pi x_k) (FP64 island)
     const T inv_n = sc[2];
