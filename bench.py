@@ -54,19 +54,25 @@ def sym_items(n: int, c: int) -> int:
 
 
 def model_flops_eval(fn: int, n: int, c: int) -> float:
-    """Model flops of one evaluation of f on hDual<c> (the Sec. V operation
-    model extended to each function's op list as the kernels state it; FMA =
-    2; a fused unary-rule accumulation acc += phi(u) counts 6c+4):
-    Rosenbrock (n-1)(18c+12) -- per term x_k^2, 100 d^2 and (1-x_k)^2;
-    Ackley n(14c+10) + 22c+18 -- per variable y_k^2 into S (6c+4) and
-    2 pi y_k, its cosine and the accumulation into Cs (8c+6), then the tail;
-    Fletcher-Powell 8n^2(c+1) + n(14c+9) -- per (m, j) two scalar-times-hDual
-    accumulations, per j sin and cos, per m the square of the residual."""
+    """Model flops of one evaluation of f on hDual<c>: every component
+    operation of each function's op list as the kernels state it, zeros of
+    the seeds included (dense), FMA = 2.  Operation costs on K = 2c+2
+    components: a unary-rule accumulation acc += phi(u) 6c+3 (6c+4 with its
+    value); scalar-times-hDual accumulation 4c+2; a unary rule 4c+2; a
+    componentwise add, negation or scaling 2c+1 or 2c+2.
+      Rosenbrock (n-1)(18c+15): per term d = x_{k+1} - x_k^2 (6c+7), then
+        100 d^2 and (1-x_k)^2 accumulated (2 x (6c+4));
+      Ackley n(12c+5) + 24c+17: per variable y_k^2/2 and cos(2 pi y_k), each
+        accumulated by the unary rule; then the tail (S = 2 (S/2), S/n, sqrt,
+        exp(-0.2 .), C/n, exp, the combination);
+      Fletcher-Powell n^2(8c+4) + n(16c+10): per (m, j) two scalar-times-hDual
+        accumulations, per j sin(y_j) and cos(y_j) (once), per m the residual
+        negated and its square accumulated."""
     if fn == 0:
-        return max(0, n - 1) * (18 * c + 12)
+        return max(0, n - 1) * (18 * c + 15)
     if fn == 1:
-        return n * (14 * c + 10) + 22 * c + 18
-    return 8 * n * n * (c + 1) + n * (14 * c + 9)
+        return n * (12 * c + 5) + 24 * c + 17
+    return n * n * (8 * c + 4) + n * (16 * c + 10)
 
 
 def model_flops_hvp(fn: int, n: int, c: int, symmetric: bool = False) -> float:
@@ -405,7 +411,7 @@ def ragged_arm(args, world, dev, stream, flush):
     from paper_2410_22575_gb300 import workloads as W
 
     rg = W.make_ragged()
-    c = 8
+    c = 16  # the plan's default chunk size for compensated FP32
     reqs = cf.requests(rg.fns, rg.ns, rg.offs, rg.eoffs)
     t0 = time.perf_counter()
     plan = cf.RaggedPlan(reqs, cf.FP32_COMP, c)

@@ -236,8 +236,9 @@ typedef struct chessfad_ragged_plan_s *chessfad_ragged_plan;
 
 /* Build a plan (host memory, owned by the caller until
  * chessfad_ragged_plan_destroy) from a host array of nreq requests for
- * precision prec with chunk size csize (8 or 16; 0 = 8).  Validates every
- * request: CHESSFAD_ERR_FUNCTION / _SIZE for a bad fn or n,
+ * precision prec with chunk size csize (8 or 16; 0 = 16 for compensated FP32,
+ * 8 for FP64).  Validates every request: CHESSFAD_ERR_FUNCTION / _SIZE for a
+ * bad fn or n,
  * CHESSFAD_ERR_PLAN for a negative offset.  Launches nothing. */
 CHESSFAD_API int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, int prec, int csize,
                                              chessfad_ragged_plan *plan);

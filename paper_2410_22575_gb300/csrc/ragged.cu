@@ -55,7 +55,10 @@ struct RaggedArgs {
 
 // The chunk sizes the uneven-batch kernel is built for; one persistent kernel
 // per (precision, chunk size) serves every function and every n.
-__host__ __device__ constexpr int ragged_mb(int C) { return C <= 8 ? 2 : 1; }
+// Fletcher-Powell residual rows held in registers per pass over the variables
+// (each seeded sin/cos hDual serves this many rows): as many as fit the
+// register file without spilling at one 256-thread CTA per SM.
+__host__ __device__ constexpr int ragged_mb(int C, bool f64) { return f64 ? (C <= 8 ? 4 : 2) : (C <= 8 ? 8 : 4); }
 
 template <typename T, int C, int FN>
 __device__ __forceinline__ void ragged_tile(const RaggedArgs &a, const RTile &t, unsigned char *smem)
@@ -80,12 +83,12 @@ __device__ __forceinline__ void ragged_tile(const RaggedArgs &a, const RTile &t,
         // entry whose terms can cancel far below their size).
         block_sweeps<double, float, 1, FN, true, 8>(job, pm, smem);
     } else {
-        block_sweeps<T, T, C, FN, true, ragged_mb(C)>(job, pm, smem);
+        block_sweeps<T, T, C, FN, true, ragged_mb(C, sizeof(T) == 8)>(job, pm, smem);
     }
 }
 
 template <typename T, int C>
-__global__ void __launch_bounds__(kRaggedBlock, sizeof(T) == 4 ? 2 : 1) ragged_kernel(const RaggedArgs a)
+__global__ void __launch_bounds__(kRaggedBlock, 1) ragged_kernel(const RaggedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_tile;
@@ -195,7 +198,7 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
     if (nreq > 0 && !reqs) return CHESSFAD_ERR_NULL;
     if (nreq > (1LL << 30)) return CHESSFAD_ERR_BATCH;
     if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
-    if (csize == 0) csize = (prec == CHESSFAD_FP64) ? 8 : 8;
+    if (csize == 0) csize = (prec == CHESSFAD_FP64) ? 8 : 16;
     if (csize != 8 && csize != 16) return CHESSFAD_ERR_CHUNK;
     for (long long q = 0; q < nreq; ++q) {
         const chessfad_request &r = reqs[q];
@@ -220,7 +223,7 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
     }
     std::vector<std::pair<double, RTile>> work;
     size_t smem = 0;
-    const int mb = ragged_mb(csize);
+    const int mb = ragged_mb(csize, prec == CHESSFAD_FP64);
     for (auto &g : groups) {
         const int fn = g.first.first, n = g.first.second;
         const int C = (prec == CHESSFAD_FP32_COMP && n == 1) ? 1 : csize;
