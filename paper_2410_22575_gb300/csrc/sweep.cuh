@@ -341,6 +341,7 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
         const AckEnt<T> *p = tab + hi;
         const AckEnt<T> *prow = tab + (i >= hi ? i : i + n);
         const int nout = n - (hi - lo);
+#pragma unroll 4
         for (int kk = 0; kk < nout; ++kk, ++p) {
             const AckEnt<T> e = *p;
             term(e, seed_at<T, C, -1>(e.x, p == prow, z));
