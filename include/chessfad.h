@@ -327,9 +327,13 @@ CHESSFAD_API int chessfad_version(void);
  * (CHESSFAD_FP32_COMP: only the row-times-v reduction is compensated; the
  * function's own sums are plain FP32 as written).
  *
- * The decomposition is one thread per (point, Hessian row), sweeping the row's
- * ceil(n/csize) chunks; x, v, out, H as for chessfad_hvp / chessfad_hessian,
- * 1 <= n <= CHESSFAD_MAX_N.
+ * Two decompositions, as for the built-in functions: plain (CHESS-VEC,
+ * Alg. 7 / CHUNK-HESS, Alg. 5: one thread per (point, Hessian row), sweeping
+ * the row's ceil(n/csize) chunks) and symmetric (SC-HESS-VEC, Alg. 8 /
+ * SCHUNK-HESS, Alg. 6: threads_per_point threads share a point's (row, chunk
+ * >= diagonal chunk) items; the HVP stages a point's chunks in shared memory,
+ * which bounds n at about 280 (FP32) / 200 (FP64)).  x, v, out, H as for
+ * chessfad_hvp / chessfad_hessian, 1 <= n <= CHESSFAD_MAX_N.
  * --------------------------------------------------------------------------- */
 typedef struct chessfad_user_fn chessfad_user_fn;
 
@@ -348,21 +352,38 @@ CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, i
 CHESSFAD_API int chessfad_user_fn_destroy(chessfad_user_fn *fn);
 
 /* The handle's chunk size and precision, and the registers per thread and
- * local (spill/stack) bytes of its HVP (hvp != 0) or Hessian kernel.  Any
- * output pointer may be NULL. */
+ * local (spill/stack) bytes of its plain HVP (hvp != 0) or Hessian kernel.
+ * Any output pointer may be NULL. */
 CHESSFAD_API int chessfad_user_fn_info(const chessfad_user_fn *fn, int hvp, int *csize, int *prec, int *registers,
                                        int *local_bytes);
 
-/* out[p] = H(x_p) v_p for the user's f (CHESS-VEC, Alg. 7), p < batch; types
- * by the handle's precision (double, or float for CHESSFAD_FP32_COMP).
- * Asynchronous on `stream`; allocates nothing. */
-CHESSFAD_API int chessfad_user_hvp(const chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
+/* out[p] = H(x_p) v_p for the user's f, p < batch; types by the handle's
+ * precision (double, or float for CHESSFAD_FP32_COMP).  The symmetric method
+ * (32 threads per point) when its staging fits shared memory, else the plain
+ * one.  Asynchronous on `stream`; allocates nothing.  The first symmetric
+ * launch on a device that needs more than 48 KiB of shared memory raises the
+ * kernel's limit (a host call; make it before capturing a CUDA graph). */
+CHESSFAD_API int chessfad_user_hvp(chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
                                    void *out, const double *params, chessfad_stream_t stream);
 
-/* H[p] = the Hessian of the user's f at x_p, every entry (CHUNK-HESS,
- * Alg. 5), [batch][n][n]. */
-CHESSFAD_API int chessfad_user_hessian(const chessfad_user_fn *fn, int n, long long batch, const void *x, void *H,
+/* H[p] = the Hessian of the user's f at x_p, every entry, [batch][n][n]
+ * (symmetric method: chunks on and above the diagonal evaluated, the rest
+ * mirrored). */
+CHESSFAD_API int chessfad_user_hessian(chessfad_user_fn *fn, int n, long long batch, const void *x, void *H,
                                        const double *params, chessfad_stream_t stream);
+
+/* As chessfad_user_hvp / chessfad_user_hessian with an explicit
+ * configuration (cfg may be NULL = the defaults above): csize 0 or the
+ * handle's (else CHESSFAD_ERR_CHUNK); method CHESSFAD_METHOD_PLAIN or
+ * _SYMMETRIC (else CHESSFAD_ERR_CONFIG); threads_per_row 0 or 1;
+ * block_threads 0 (= 256) or 32..256, a multiple of 32; threads_per_point 0
+ * (= 32) or 32..256, a power of two.  A symmetric HVP whose staging does not
+ * fit shared memory returns CHESSFAD_ERR_SIZE. */
+CHESSFAD_API int chessfad_user_hvp_config(chessfad_user_fn *fn, int n, long long batch, const chessfad_config *cfg,
+                                          const void *x, const void *v, void *out, const double *params,
+                                          chessfad_stream_t stream);
+CHESSFAD_API int chessfad_user_hessian_config(chessfad_user_fn *fn, int n, long long batch, const chessfad_config *cfg,
+                                              const void *x, void *H, const double *params, chessfad_stream_t stream);
 
 #ifdef __cplusplus
 }

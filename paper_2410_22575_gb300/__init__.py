@@ -97,8 +97,11 @@ def load(build_if_missing: bool = True):
                                               ctypes.POINTER(I)]
         lib.chessfad_user_hvp.argtypes = [P, I, L, P, P, P, P, P]
         lib.chessfad_user_hessian.argtypes = [P, I, L, P, P, P, P]
+        lib.chessfad_user_hvp_config.argtypes = [P, I, L, P, P, P, P, P, P]
+        lib.chessfad_user_hessian_config.argtypes = [P, I, L, P, P, P, P, P]
         for name in ("chessfad_user_fn_create", "chessfad_user_fn_destroy", "chessfad_user_fn_info",
-                     "chessfad_user_hvp", "chessfad_user_hessian"):
+                     "chessfad_user_hvp", "chessfad_user_hessian", "chessfad_user_hvp_config",
+                     "chessfad_user_hessian_config"):
             getattr(lib, name).restype = I
         lib.chessfad_hvp_host.argtypes = [I, I, L, I, P, P, P, P, P, P, P, I, I, P]
         lib.chessfad_hvp_host.restype = I
@@ -384,6 +387,18 @@ def chessfad_user_hessian(handle, n, batch, x, H, params=None, stream=None) -> i
     return load().chessfad_user_hessian(handle, n, batch, _addr(x), _addr(H), _addr(params), _stream(stream))
 
 
+def chessfad_user_hvp_config(handle, n, batch, cfg, x, v, out, params=None, stream=None) -> int:
+    c = ctypes.byref(cfg) if cfg is not None else None
+    return load().chessfad_user_hvp_config(handle, n, batch, c, _addr(x), _addr(v), _addr(out), _addr(params),
+                                           _stream(stream))
+
+
+def chessfad_user_hessian_config(handle, n, batch, cfg, x, H, params=None, stream=None) -> int:
+    c = ctypes.byref(cfg) if cfg is not None else None
+    return load().chessfad_user_hessian_config(handle, n, batch, c, _addr(x), _addr(H), _addr(params),
+                                               _stream(stream))
+
+
 class UserFunction:
     """A user-supplied f compiled for one chunk size and precision.  ``source``
     defines ``template <class R, class X> R name(const X &x, int n, const
@@ -399,22 +414,23 @@ class UserFunction:
     def info(self, hvp=True) -> dict:
         return chessfad_user_fn_info(self.handle, hvp)
 
-    def hvp(self, x, v, params=None, stream=None, out=None):
+    def hvp(self, x, v, params=None, stream=None, out=None, cfg=None):
         import torch
 
         batch, n = x.shape
         if out is None:
             out = torch.empty_like(x)
-        _check(chessfad_user_hvp(self.handle, n, batch, x, v, out, params, stream), "chessfad_user_hvp")
+        _check(chessfad_user_hvp_config(self.handle, n, batch, cfg, x, v, out, params, stream), "chessfad_user_hvp")
         return out
 
-    def hessian(self, x, params=None, stream=None, out=None):
+    def hessian(self, x, params=None, stream=None, out=None, cfg=None):
         import torch
 
         batch, n = x.shape
         if out is None:
             out = torch.empty((batch, n, n), dtype=x.dtype, device=x.device)
-        _check(chessfad_user_hessian(self.handle, n, batch, x, out, params, stream), "chessfad_user_hessian")
+        _check(chessfad_user_hessian_config(self.handle, n, batch, cfg, x, out, params, stream),
+               "chessfad_user_hessian")
         return out
 
     def close(self):

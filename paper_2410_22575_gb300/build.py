@@ -50,7 +50,8 @@ def up_to_date() -> bool:
 
 # Sources compiled at run time (NVRTC) for user-supplied functions, embedded
 # in the library as string constants: (C++ name, file under csrc/).
-EMBEDDED = (("kHdualSrc", "hdual.cuh"), ("kUserNumSrc", "user_num.cuh"), ("kUserKernelSrc", "user_kernel.cuh"))
+EMBEDDED = (("kHdualSrc", "hdual.cuh"), ("kSymLayoutSrc", "sym_layout.cuh"), ("kUserNumSrc", "user_num.cuh"),
+            ("kUserKernelSrc", "user_kernel.cuh"))
 DELIM = "CHESSFAD_EMBED"
 
 

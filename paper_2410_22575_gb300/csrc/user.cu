@@ -21,14 +21,18 @@
 #include <vector>
 
 #include "../../include/chessfad.h"
-#include "user_embed.h"  // generated by the build: kHdualSrc, kUserNumSrc, kUserKernelSrc
+#include "user_embed.h"  // generated by the build: kHdualSrc, kSymLayoutSrc, kUserNumSrc, kUserKernelSrc
 
 struct chessfad_user_fn {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t hvp = nullptr;
-    cudaKernel_t hessian = nullptr;
+    cudaKernel_t hvp = nullptr;          // plain (CHESS-VEC, Alg. 7)
+    cudaKernel_t hessian = nullptr;      // plain (CHUNK-HESS, Alg. 5)
+    cudaKernel_t sym_hvp = nullptr;      // symmetric (SC-HESS-VEC, Alg. 8)
+    cudaKernel_t sym_hessian = nullptr;  // symmetric (SCHUNK-HESS, Alg. 6)
     int csize = 0;
     int prec = 0;
+    std::mutex mu;
+    unsigned long long smem_opted = 0;  // bit d: the symmetric kernels' shared-memory limit raised on device d
 };
 
 namespace {
@@ -103,34 +107,112 @@ bool is_identifier(const char *s)
 bool valid_chunk(int c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
 constexpr int kBlock = 256;
+constexpr size_t kSmemBudget = 200 * 1024;  // symmetric kernels' dynamic shared memory ceiling
 
-int launch(const chessfad_user_fn *fn, bool hvp, int n, long long batch, const void *x, const void *v, void *out,
-           const double *params, cudaStream_t stream)
+struct UserArgs {  // the kernels' chessfad::user::UserArgs, field for field
+    const void *x;
+    const void *v;
+    void *out;
+    long long batch;
+    const double *params;
+    int n;
+    int maxpts;
+    int tpp;
+};
+
+long long hs_elems(int n, int C)  // staged chunk matrix of one point, symmetric HVP
+{
+    const long long nch = (n + C - 1) / C;
+    return C * (nch * (n + 1) - C * nch * (nch - 1) / 2);
+}
+
+// Resolve a launch configuration for a handle: method 0 = plain, 1 =
+// symmetric; -1 = symmetric when its shared memory fits, else plain.
+int resolve(const chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, int n, long long batch, int &method,
+            int &bt, int &tpp, int &ppb, size_t &smem)
+{
+    const size_t elem = fn->prec == CHESSFAD_FP64 ? sizeof(double) : sizeof(float);
+    method = -1;
+    bt = 0;
+    tpp = 0;
+    if (cfg) {
+        if (cfg->csize != 0 && cfg->csize != fn->csize) return CHESSFAD_ERR_CHUNK;
+        if (cfg->method != CHESSFAD_METHOD_PLAIN && cfg->method != CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_CONFIG;
+        if (cfg->threads_per_row > 1) return CHESSFAD_ERR_CONFIG;
+        if (cfg->block_threads != 0 && (cfg->block_threads < 32 || cfg->block_threads > 256 || cfg->block_threads % 32))
+            return CHESSFAD_ERR_CONFIG;
+        const int p = cfg->threads_per_point;
+        if (p != 0 && (p < 32 || p > 256 || (p & (p - 1)))) return CHESSFAD_ERR_CONFIG;
+        method = cfg->method;
+        bt = cfg->block_threads;
+        tpp = p;
+    }
+    if (bt == 0) bt = kBlock;
+    if (tpp == 0) tpp = 32;
+    if (method != CHESSFAD_METHOD_PLAIN) {
+        if (tpp > bt) bt = tpp;
+        const size_t per_pt = ((size_t)n * (hvp ? 2 : 1) + (hvp ? (size_t)hs_elems(n, fn->csize) : 0)) * elem;
+        long long p = bt / tpp;
+        if (p > batch) p = batch;
+        while (p > 1 && (size_t)p * per_pt > kSmemBudget) --p;
+        if ((size_t)p * per_pt <= kSmemBudget) {
+            method = CHESSFAD_METHOD_SYMMETRIC;
+            ppb = (int)p;
+            smem = (size_t)p * per_pt;
+            return CHESSFAD_SUCCESS;
+        }
+        if (method == CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_SIZE;
+    }
+    method = CHESSFAD_METHOD_PLAIN;
+    const long long per_cta = (bt - 1) / n + 2;
+    ppb = (int)(batch < per_cta ? batch : per_cta);
+    smem = (size_t)ppb * n * elem * 2;
+    return CHESSFAD_SUCCESS;
+}
+
+int launch(chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, int n, long long batch, const void *x,
+           const void *v, void *out, const double *params, cudaStream_t stream)
 {
     if (!fn || !fn->lib) return CHESSFAD_ERR_NULL;
     if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
     if (batch < 0) return CHESSFAD_ERR_BATCH;
+    int method, bt, tpp, ppb = 0;
+    size_t smem = 0;
+    int st = resolve(fn, cfg, hvp, n, batch > 0 ? batch : 1, method, bt, tpp, ppb, smem);
+    if (st != CHESSFAD_SUCCESS) return st;
     if (batch == 0) return CHESSFAD_SUCCESS;
     if (!x || !out || (hvp && !v)) return CHESSFAD_ERR_NULL;
-    const long long items = batch * (long long)n;
-    const long long grid = (items + kBlock - 1) / kBlock;
+    UserArgs args{x, hvp ? v : x, out, batch, params, n, ppb, tpp};
+    long long grid;
+    unsigned block;
+    cudaKernel_t k;
+    if (method == CHESSFAD_METHOD_SYMMETRIC) {
+        grid = (batch + ppb - 1) / ppb;
+        block = (unsigned)(ppb * tpp);
+        k = hvp ? fn->sym_hvp : fn->sym_hessian;
+        if (smem > 48 * 1024) {
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
+            std::lock_guard<std::mutex> lk(fn->mu);
+            const unsigned long long bit = 1ull << (dev & 63);
+            if (!(fn->smem_opted & bit)) {
+                for (cudaKernel_t kk : {fn->sym_hvp, fn->sym_hessian})
+                    if (cudaFuncSetAttribute(reinterpret_cast<const void *>(kk),
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget) !=
+                        cudaSuccess)
+                        return CHESSFAD_ERR_CUDA;
+                fn->smem_opted |= bit;
+            }
+        }
+    } else {
+        grid = (batch * (long long)n + bt - 1) / bt;
+        block = (unsigned)bt;
+        k = hvp ? fn->hvp : fn->hessian;
+    }
     if (grid > 0x7fffffffLL) return CHESSFAD_ERR_BATCH;
-    struct {
-        const void *x;
-        const void *v;
-        void *out;
-        long long batch;
-        const double *params;
-        int n;
-        int maxpts;
-    } args{x, hvp ? v : x, out, batch, params, n, 0};
-    const long long per_cta = (kBlock - 1) / n + 2;
-    args.maxpts = (int)(batch < per_cta ? batch : per_cta);
-    const size_t elem = fn->prec == CHESSFAD_FP64 ? sizeof(double) : sizeof(float);
-    const size_t smem = (size_t)args.maxpts * n * elem * 2;
     void *argv[] = {&args};
-    cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void *>(hvp ? fn->hvp : fn->hessian),
-                                     dim3((unsigned)grid), dim3(kBlock), argv, smem, stream);
+    cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void *>(k), dim3((unsigned)grid), dim3(block), argv, smem,
+                                     stream);
     return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
 }
 
@@ -158,10 +240,10 @@ CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, i
     std::string text = "#include \"user_num.cuh\"\n#line 1 \"user_function\"\n";
     text += source;
     text += "\n#include \"user_kernel.cuh\"\n";
-    const char *headers[] = {kHdualSrc, kUserNumSrc, kUserKernelSrc, ""};
-    const char *header_names[] = {"hdual.cuh", "user_num.cuh", "user_kernel.cuh", "cuda_runtime.h"};
+    const char *headers[] = {kHdualSrc, kSymLayoutSrc, kUserNumSrc, kUserKernelSrc, ""};
+    const char *header_names[] = {"hdual.cuh", "sym_layout.cuh", "user_num.cuh", "user_kernel.cuh", "cuda_runtime.h"};
     nvrtcProgram prog = nullptr;
-    if (rt.create(&prog, text.c_str(), "chessfad_user.cu", 4, headers, header_names) != NVRTC_SUCCESS) {
+    if (rt.create(&prog, text.c_str(), "chessfad_user.cu", 5, headers, header_names) != NVRTC_SUCCESS) {
         put_log(log, log_bytes, "nvrtcCreateProgram failed");
         return CHESSFAD_ERR_JIT;
     }
@@ -198,6 +280,8 @@ CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, i
     cudaError_t e = cudaLibraryLoadData(&fn->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->hvp, fn->lib, "chessfad_user_hvp");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->hessian, fn->lib, "chessfad_user_hessian");
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->sym_hvp, fn->lib, "chessfad_user_sym_hvp");
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->sym_hessian, fn->lib, "chessfad_user_sym_hessian");
     if (e != cudaSuccess) {
         cudaGetLastError();
         put_log(log, log_bytes, std::string("compiled; loading failed: ") + cudaGetErrorString(e));
@@ -231,16 +315,29 @@ CHESSFAD_API int chessfad_user_fn_info(const chessfad_user_fn *fn, int hvp, int 
     return CHESSFAD_SUCCESS;
 }
 
-CHESSFAD_API int chessfad_user_hvp(const chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
+CHESSFAD_API int chessfad_user_hvp(chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
                                    void *out, const double *params, chessfad_stream_t stream)
 {
-    return launch(fn, true, n, batch, x, v, out, params, reinterpret_cast<cudaStream_t>(stream));
+    return launch(fn, nullptr, true, n, batch, x, v, out, params, reinterpret_cast<cudaStream_t>(stream));
 }
 
-CHESSFAD_API int chessfad_user_hessian(const chessfad_user_fn *fn, int n, long long batch, const void *x, void *H,
+CHESSFAD_API int chessfad_user_hessian(chessfad_user_fn *fn, int n, long long batch, const void *x, void *H,
                                        const double *params, chessfad_stream_t stream)
 {
-    return launch(fn, false, n, batch, x, nullptr, H, params, reinterpret_cast<cudaStream_t>(stream));
+    return launch(fn, nullptr, false, n, batch, x, nullptr, H, params, reinterpret_cast<cudaStream_t>(stream));
+}
+
+CHESSFAD_API int chessfad_user_hvp_config(chessfad_user_fn *fn, int n, long long batch, const chessfad_config *cfg,
+                                          const void *x, const void *v, void *out, const double *params,
+                                          chessfad_stream_t stream)
+{
+    return launch(fn, cfg, true, n, batch, x, v, out, params, reinterpret_cast<cudaStream_t>(stream));
+}
+
+CHESSFAD_API int chessfad_user_hessian_config(chessfad_user_fn *fn, int n, long long batch, const chessfad_config *cfg,
+                                              const void *x, void *H, const double *params, chessfad_stream_t stream)
+{
+    return launch(fn, cfg, false, n, batch, x, nullptr, H, params, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -6,14 +6,22 @@
 //   CHESSFAD_USER_FN   the name of the user's function template
 //                        template <class R, class X>
 //                        R name(const X &x, int n, const double *params);
-// Decomposition (the paper's L2 over rows, Sec. VI): one thread per
-// (point, row i), sweeping the row's ceil(n/C) chunks; a CTA of 256 threads
-// stages the x (and v) of the points its rows belong to in shared memory.
+// Two decompositions:
+//  plain (CHESS-VEC / CHUNK-HESS, the paper's L2 over rows, Sec. VI): one
+//    thread per (point, row i), sweeping the row's ceil(n/C) chunks; a CTA
+//    stages the x (and v) of the points its rows belong to in shared memory;
+//  symmetric (SC-HESS-VEC, Alg. 8 / SCHUNK-HESS, Alg. 6): a CTA holds maxpts
+//    points with tpp threads each; a point's items (row i, chunk cn >=
+//    floor(i/C)) are dealt round-robin to its threads.  The Hessian writes
+//    each chunk and its mirror image; the HVP stages the chunks in shared
+//    memory (compact upper-block layout) and, after one barrier, every thread
+//    sums whole rows, each off-diagonal-chunk entry serving both r_i and r_j.
 // FP32: the row-times-v products are summed as a Dot2 (TwoProd by FMA plus
 // TwoSum); the function's own arithmetic is plain FP32, as written by the
 // user.  FP64: fused multiply-add accumulation.
 #pragma once
 
+#include "sym_layout.cuh"
 #include "user_num.cuh"
 
 namespace chessfad {
@@ -26,7 +34,9 @@ struct UserArgs {
     long long batch;
     const double *params;
     int n;
-    int maxpts;  // points staged per CTA: min(batch, 255 / n + 2)
+    int maxpts;  // plain: points staged per CTA, min(batch, (blockDim - 1) / n + 2);
+                 // symmetric: points per CTA
+    int tpp;     // symmetric: threads per point
 };
 
 template <typename T>
@@ -90,8 +100,87 @@ __device__ __forceinline__ void user_sweep(const UserArgs &a)
     if (HVP) static_cast<T *>(a.out)[p * n + i] = dot.value();
 }
 
+template <typename T, int C, bool HVP>
+__device__ __forceinline__ void user_sym(const UserArgs &a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, ppb = a.maxpts, tpp = a.tpp;
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    T *vs = xs + (size_t)ppb * n;
+    T *hs = vs + (HVP ? (size_t)ppb * n : 0);
+    const long long p0 = (long long)blockIdx.x * ppb;
+    const int npts = (int)(a.batch - p0 < ppb ? a.batch - p0 : ppb);
+    const T *xg = static_cast<const T *>(a.x) + p0 * n;
+    const T *vg = static_cast<const T *>(a.v) + p0 * n;
+    for (int e = threadIdx.x; e < npts * n; e += blockDim.x) {
+        xs[e] = xg[e];
+        if (HVP) vs[e] = vg[e];
+    }
+    __syncthreads();
+    const int q = threadIdx.x / tpp, t = threadIdx.x - q * tpp;
+    const bool active = q < npts;
+    const long long p = p0 + q;
+    const T *xp = xs + (size_t)q * n;
+    T *Hs = hs + (size_t)q * sym_hs_elems(n, C);
+    const T z = opaque_zero<T>();
+    const int nch = (n + C - 1) / C;
+    const int items = C * nch * (nch + 1) / 2;
+    for (int k = active ? t : items; k < items; k += tpp) {
+        int i = 0, cn = 0;
+        sym_item(k, C, nch, i, cn);
+        if (i >= n) continue;
+        const int cstart = cn * C;
+        const Vars<T, C> x{xp, i, cstart, z};
+        const Num<T, C> r = ::CHESSFAD_USER_FN<Num<T, C>, Vars<T, C>>(x, n, a.params);
+        if (HVP) {
+            T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
+#pragma unroll
+            for (int l = 0; l < C; ++l)
+                if (cstart + l < n) hrow[cstart + l] = r.a.h[l];
+        } else {
+            T *H = static_cast<T *>(a.out) + (size_t)p * n * n;
+            const bool mirror = cn > i / C;
+#pragma unroll
+            for (int l = 0; l < C; ++l) {
+                const int j = cstart + l;
+                if (j < n) {
+                    H[(size_t)i * n + j] = r.a.h[l];
+                    if (mirror) H[(size_t)j * n + i] = r.a.h[l];
+                }
+            }
+        }
+    }
+    if (HVP) {
+        // r_s = sum_j H_sj v_j: entries right of row s's diagonal chunk from
+        // row s, entries left of it from column s (H_sj = H_js).
+        __syncthreads();
+        if (active) {
+            const T *vp = vs + (size_t)q * n;
+            T *O = static_cast<T *>(a.out) + p * n;
+            for (int srow = t; srow < n; srow += tpp) {
+                const int dstart = (srow / C) * C;
+                const T *own = Hs + sym_hs_row(srow, n, C) - dstart;
+                RowDot<T> dot;
+                for (int j = 0; j < dstart; ++j) dot.add(Hs[sym_hs_row(j, n, C) + srow - (j / C) * C], vp[j]);
+                for (int j = dstart; j < n; ++j) dot.add(own[j], vp[j]);
+                O[srow] = dot.value();
+            }
+        }
+    }
+}
+
 }  // namespace user
 }  // namespace chessfad
+
+extern "C" __global__ void __launch_bounds__(256) chessfad_user_sym_hvp(chessfad::user::UserArgs a)
+{
+    chessfad::user::user_sym<CHESSFAD_USER_T, CHESSFAD_USER_C, true>(a);
+}
+
+extern "C" __global__ void __launch_bounds__(256) chessfad_user_sym_hessian(chessfad::user::UserArgs a)
+{
+    chessfad::user::user_sym<CHESSFAD_USER_T, CHESSFAD_USER_C, false>(a);
+}
 
 extern "C" __global__ void __launch_bounds__(256) chessfad_user_hvp(chessfad::user::UserArgs a)
 {

@@ -71,17 +71,23 @@ class Case:
         return metrics.hessian_errors(H.double().cpu().numpy(), oracle.hessian_batch(self.fn, self.xh, self.oparams))
 
 
+PLAIN = cf.Config(0, 1, 256, cf.PLAIN, 0)
+SYM = cf.Config(0, 0, 0, cf.SYMMETRIC, 32)
+
+
 @pytest.mark.parametrize("fn", FNS)
 @pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
 @pytest.mark.parametrize("c", [1, 4, 8, 16])
 def test_user_hvp_and_hessian(fn, prec, c):
-    """n = 19: ragged last chunk; 70 points: several CTAs and a partial one."""
+    """n = 19: ragged last chunk; 70 points: several CTAs and a partial one;
+    plain (Alg. 7 / Alg. 5), symmetric (Alg. 8 / Alg. 6) and the default."""
     f = user_fn(fn, c, prec)
     k = Case(fn, 19, 70, 900 + c, prec)
-    e = k.hvp_err(f.hvp(k.x, k.v, k.params))
-    assert e.max() <= BOUND[prec][fn], (e.max(), np.median(e))
-    e = k.hess_err(f.hessian(k.x, k.params))
-    assert e.max() <= BOUND[prec][fn], (e.max(), np.median(e))
+    for cfg in (PLAIN, SYM, cf.Config(0, 0, 128, cf.SYMMETRIC, 64), None):
+        e = k.hvp_err(f.hvp(k.x, k.v, k.params, cfg=cfg))
+        assert e.max() <= BOUND[prec][fn], (cfg, e.max(), np.median(e))
+        e = k.hess_err(f.hessian(k.x, k.params, cfg=cfg))
+        assert e.max() <= BOUND[prec][fn], (cfg, e.max(), np.median(e))
 
 
 @pytest.mark.parametrize("fn", FNS)
@@ -90,8 +96,9 @@ def test_user_sizes(fn, n):
     for prec in (cf.FP64, cf.FP32_COMP):
         f = user_fn(fn, 8, prec)
         k = Case(fn, n, 37 if n < 100 else 5, 950 + n, prec)
-        e = k.hvp_err(f.hvp(k.x, k.v, k.params))
-        assert e.max() <= bound(prec, fn, n), (prec, e.max())
+        for cfg in (PLAIN, None):
+            e = k.hvp_err(f.hvp(k.x, k.v, k.params, cfg=cfg))
+            assert e.max() <= bound(prec, fn, n), (prec, cfg, e.max())
 
 
 def test_user_equals_builtin_fp64():
@@ -139,3 +146,43 @@ def test_user_compile_error_on_device():
     st, handle, log = cf.chessfad_user_fn_create(
         "template <class R, class X> R g(const X &x, int n, const double *p) { return x[0] * ; }", "g", 8, cf.FP64)
     assert st == -12 and handle is None and "error" in log
+
+
+def test_user_symmetric_limits_and_config_errors():
+    import torch
+
+    f = user_fn(W.ROSENBROCK, 8, cf.FP64)
+    k = Case(W.ROSENBROCK, 300, 3, 17, cf.FP64)
+    out = torch.empty_like(k.x)
+    # the symmetric HVP's staging does not fit: explicit request rejected,
+    # the default falls back to the plain method
+    assert cf.chessfad_user_hvp_config(f.handle, 300, 3, SYM, k.x, k.v, out) == -2
+    assert k.hvp_err(f.hvp(k.x, k.v)).max() <= 1e-12
+    # the symmetric Hessian has no staging limit
+    assert k.hess_err(f.hessian(k.x, cfg=SYM)).max() <= 1e-12
+    for bad, code in ((cf.Config(4, 0, 0, cf.PLAIN, 0), -4), (cf.Config(0, 0, 0, cf.SYMMETRIC_SPARSE, 0), -9),
+                      (cf.Config(0, 2, 0, cf.PLAIN, 0), -9), (cf.Config(0, 0, 48, cf.PLAIN, 0), -9),
+                      (cf.Config(0, 0, 0, cf.SYMMETRIC, 48), -9)):
+        assert cf.chessfad_user_hvp_config(f.handle, 300, 3, bad, k.x, k.v, out) == code, bad
+
+
+def test_user_symmetric_faster_than_plain_on_ackley():
+    """SC-HESS-VEC does about half the evaluations of CHESS-VEC (Sec. V)."""
+    import torch
+
+    f = user_fn(W.ACKLEY, 8, cf.FP32_COMP)
+    k = Case(W.ACKLEY, 64, 8192, 3, cf.FP32_COMP)
+    out = torch.empty_like(k.x)
+
+    def t(cfg):
+        f.hvp(k.x, k.v, out=out, cfg=cfg)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            f.hvp(k.x, k.v, out=out, cfg=cfg)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    assert t(SYM) < 0.85 * t(PLAIN)
