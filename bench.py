@@ -62,16 +62,17 @@ def model_flops_eval(fn: int, n: int, c: int) -> float:
     componentwise add, negation or scaling 2c+1 or 2c+2.
       Rosenbrock (n-1)(18c+15): per term d = x_{k+1} - x_k^2 (6c+7), then
         100 d^2 and (1-x_k)^2 accumulated (2 x (6c+4));
-      Ackley n(12c+5) + 24c+17: per variable y_k^2/2 and cos(2 pi y_k), each
-        accumulated by the unary rule; then the tail (S = 2 (S/2), S/n, sqrt,
-        exp(-0.2 .), C/n, exp, the combination);
+      Ackley n(12c+5) + 14c+17: per variable y_k^2/2 and cos(2 pi y_k), each
+        accumulated by the unary rule; then the tail, three unary rules with
+        the constant factors folded into phi' and phi'' (sqrt(S/n) of S/2,
+        -20 exp(-0.2 r), -exp(C/n) accumulated);
       Fletcher-Powell n^2(8c+4) + n(16c+10): per (m, j) two scalar-times-hDual
         accumulations, per j sin(y_j) and cos(y_j) (once), per m the residual
         negated and its square accumulated."""
     if fn == 0:
         return max(0, n - 1) * (18 * c + 15)
     if fn == 1:
-        return n * (12 * c + 5) + 24 * c + 17
+        return n * (12 * c + 5) + 14 * c + 17
     return n * n * (8 * c + 4) + n * (16 * c + 10)
 
 

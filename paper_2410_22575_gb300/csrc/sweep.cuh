@@ -371,15 +371,19 @@ __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ t
             term(e, seed<T, C>(e.x, k, i, cstart, z));
         }
     }
-    HD<T, C> S = smul(T(2), Sh);
-    S.v = sc[0];   // sum x_k^2        (FP64 island)
-    Cs.v = sc[1];  // sum cos(2 pi x_k) (FP64 island)
+    // The tail, each step one unary rule with the constant factors folded
+    // into phi' and phi'' (the per-point values come from the FP64 island
+    // sums: sc[3] = sqrt(S/n) with its derivatives sc[4], sc[5]; sc[6] =
+    // exp(-0.2 sqrt(S/n)); sc[7] = exp(Cs/n)):
+    //   r  = sqrt(S/n) as a function of Sh = S/2: phi' = (2/n) sc[4], phi'' = (2/n)^2 sc[5]
+    //   f  = -20 exp(-0.2 r) as a function of r:  phi' = 4 sc[6], phi'' = -0.8 sc[6]
+    //   f += -exp(Cs/n) as a function of Cs:      phi' = -sc[7]/n, phi'' = -sc[7]/n^2
     const T inv_n = sc[2];
-    const HD<T, C> a = smul(inv_n, S);                   // S/n
-    const HD<T, C> r = unary(a, sc[3], sc[4], sc[5]);    // sqrt(S/n)
-    const HD<T, C> t1 = unary(smul(T(-0.2), r), sc[6], sc[6], sc[6]);  // exp(-0.2 r)
-    const HD<T, C> t2 = unary(smul(inv_n, Cs), sc[7], sc[7], sc[7]);   // exp(Cs/n)
-    HD<T, C> f = hsub(smul(T(-20), t1), t2);
+    const T k2 = T(2) * inv_n;
+    const HD<T, C> r = unary(Sh, sc[3], k2 * sc[4], (k2 * k2) * sc[5]);
+    const T e1 = sc[6], e2 = sc[7];
+    HD<T, C> f = unary(r, T(-20) * e1, T(4) * e1, T(-0.8) * e1);
+    add_unary<true>(f, Cs, -e2, -inv_n * e2, -(inv_n * inv_n) * e2);
     f.v = f.v + T(20) + T(2.718281828459045);
     return f;
 }
