@@ -396,9 +396,13 @@ def gpu_arm(args):
 
 
 # ------------------------------------------------------------------ uneven batch
+RAGGED_SYM_MIN_N = 128  # Fletcher-Powell requests this large run the symmetric method
+
+
 def model_flops_request(fn: int, n: int, c: int) -> float:
-    """Model flops of one HVP of the uneven batch (plain method)."""
-    return model_flops_hvp(fn, n, c)
+    """Model flops of one HVP of the uneven batch: the symmetric method for
+    Fletcher-Powell requests with n >= 128, the plain method otherwise."""
+    return model_flops_hvp(fn, n, c, fn == 2 and n >= RAGGED_SYM_MIN_N)
 
 
 def ragged_arm(args, world, dev, stream, flush):
@@ -439,6 +443,7 @@ def ragged_arm(args, world, dev, stream, flush):
     return {"value": world * rg.nreq * len(ms) / (tot * 1e-3), "unit": "HVP/s", "requests": rg.nreq,
             "steps": len(ms), "warmup": 1, "ms_per_step": per, "precision": "fp32_comp", "csize": c,
             "launch": "one persistent kernel per step, CUDA graph replay", "tiles": plan.info["ntiles"],
+            "method": "plain; symmetric (SC-HESS-VEC) for Fletcher-Powell n >= 128",
             "workspace_bytes": plan.info["workspace_bytes"], "plan_seconds": t_plan,
             "model_tflops": flops / (per * 1e-3) / 1e12,
             "_out": out, "_x": x, "_v": v, "_rg": rg}

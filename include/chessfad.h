@@ -244,9 +244,10 @@ CHESSFAD_API int chessfad_ragged_plan_create(const chessfad_request *reqs, long 
                                              chessfad_ragged_plan *plan);
 CHESSFAD_API int chessfad_ragged_plan_destroy(chessfad_ragged_plan plan);
 
-/* Device workspace bytes the plan needs (tile table, request list, offsets and
- * the queue counter), the number of tiles and the dynamic shared memory per
- * CTA.  Any pointer may be NULL. */
+/* Device workspace bytes the plan needs (tile table, request list, offsets,
+ * the queue counter, and for the Fletcher-Powell requests with n >= 128 a row
+ * counter and n FP64 accumulators each), the number of tiles and the dynamic
+ * shared memory per CTA.  Any pointer may be NULL. */
 CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes, long long *ntiles,
                                            size_t *smem_bytes);
 
@@ -256,9 +257,16 @@ CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *wo
 CHESSFAD_API int chessfad_ragged_plan_upload(chessfad_ragged_plan plan, void *workspace, size_t workspace_bytes,
                                              chessfad_stream_t stream);
 
-/* Run the plan: reset the queue counter in the workspace (cudaMemsetAsync) and
- * launch one persistent kernel, both on stream; no host synchronisation, no
- * allocation, so the call can be captured into a CUDA graph and replayed.
+/* Run the plan: reset the queue counter, row counters and accumulators in the
+ * workspace (one cudaMemsetAsync) and launch one persistent kernel, both on
+ * stream; no host synchronisation, no allocation, so the call can be captured
+ * into a CUDA graph and replayed.  Fletcher-Powell requests with n >= 128 use
+ * the symmetric method (SC-HESS-VEC, Alg. 8; about half the evaluations):
+ * each entry right of a row's diagonal chunk also updates the row it mirrors,
+ * usually in another tile, through FP64 atomic adds, and the tile finishing a
+ * request's last rows rounds its accumulators into outpack.  The FP64
+ * addition order varies, so FP64 results of those requests can differ from
+ * run to run in the last bits; everything else is bitwise reproducible.
  * xpack, vpack, outpack: device, float (FP32_COMP) or double (FP64) by the
  * plan's precision.  params: required when the plan holds Fletcher-Powell
  * requests (ld >= their largest n).  Runs that share a workspace must not
@@ -273,19 +281,20 @@ CHESSFAD_API int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpac
  * device, or real-time code with no room for allocation latency.  The paper
  * has no counterpart; it is a deployment convenience.
  *
- * The scratch (the plan's tables and the queue counter) lives in a static
- * device array of CHESSFAD_RAGGED_STATIC_BYTES that every GPU which loads the
- * library holds until the process exits.  Each call copies the plan's tables
- * and a zeroed counter into it (cudaMemcpyAsync on stream) and launches the
- * persistent kernel; it allocates nothing and calls no allocating routine.
+ * The scratch (the plan's tables, counters and accumulators) lives in a
+ * static device array of CHESSFAD_RAGGED_STATIC_BYTES that every GPU which
+ * loads the library holds until the process exits.  Each call copies the
+ * plan's tables into it (cudaMemcpyAsync on stream), zeroes the counters and
+ * accumulators (cudaMemsetAsync) and launches the persistent kernel; it
+ * allocates nothing and calls no allocating routine.
  * The first call on a device also looks up the array's device address on
  * that device (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array, so calls whose work overlaps on
  * the GPU (other streams, other host threads) race; serialise them.
- * Returns CHESSFAD_ERR_WORKSPACE if the plan's tables exceed
+ * Returns CHESSFAD_ERR_WORKSPACE if the plan's workspace exceeds
  * CHESSFAD_RAGGED_STATIC_BYTES (chessfad_ragged_plan_info reports the
  * size); other arguments and errors as chessfad_hvp_ragged. */
-#define CHESSFAD_RAGGED_STATIC_BYTES (8u << 20)
+#define CHESSFAD_RAGGED_STATIC_BYTES (32u << 20)
 CHESSFAD_API int chessfad_hvp_ragged_noalloc(chessfad_ragged_plan plan, const void *xpack, const void *vpack,
                                              void *outpack, const chessfad_fp_params *params,
                                              chessfad_stream_t stream);

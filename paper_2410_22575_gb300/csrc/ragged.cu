@@ -11,8 +11,20 @@
 //
 // Device side: a persistent kernel, a few CTAs per SM, whose CTAs take tile
 // after tile from the counter with atomicAdd and run the tile's sweeps.  No
-// CTA ever waits for another one.  A run is {memset of the counter, kernel},
-// both stream-ordered, so it can be captured into a CUDA graph and replayed.
+// CTA ever waits for another one.  A run is {memset of the counter and the
+// accumulators, kernel}, both stream-ordered, so it can be captured into a
+// CUDA graph and replayed.
+//
+// Fletcher-Powell requests with n >= kSymMinN (where nearly all of the cost
+// is) use the symmetric method, SC-HESS-VEC (Alg. 8): row i evaluates only
+// the chunks from its diagonal chunk on, about half the evaluations.  Each
+// off-diagonal-chunk entry H_ij serves r_i in the row's own sum and r_j,
+// a row usually in another tile, so both go into an FP64 accumulator per
+// request element with atomic adds (the products of two FP32 values are
+// exact in FP64); the tile that completes a request's last rows (a per-
+// request row counter) rounds the accumulators into the output.  The FP64
+// addition order varies between runs, so these results may differ in the
+// last FP64 bits; FP32 outputs are the rounding of an FP64 sum.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,9 +45,12 @@ struct RTile {
     long long npoints;  // points (requests) in the group
     int list0;          // group's first entry in the request list
     int fn, n, nch, tpr, maxpts, mt;
+    int sym;            // symmetric tile: rows row0 .. row0+nrows-1 of one point
+    int nrows;
 };
 
 constexpr int kRaggedBlock = 256;
+constexpr int kSymMinN = 128;  // Fletcher-Powell requests this large use the symmetric method
 
 struct RaggedArgs {
     const void *x;
@@ -48,7 +63,10 @@ struct RaggedArgs {
     const int *list;
     const long long *offs;
     const long long *eoffs;
+    const long long *soffs;  // per request: first accumulator element (symmetric requests)
     int *counter;
+    int *done;               // per request: rows completed (symmetric requests)
+    double *acc;             // FP64 accumulators of the symmetric requests
     int ntiles;
     int ld;
 };
@@ -59,6 +77,84 @@ struct RaggedArgs {
 // (each seeded sin/cos hDual serves this many rows): as many as fit the
 // register file without spilling at one 256-thread CTA per SM.
 __host__ __device__ constexpr int ragged_mb(int C, bool f64) { return f64 ? (C <= 8 ? 4 : 2) : (C <= 8 ? 8 : 4); }
+
+// One symmetric tile: rows i0 .. i0+nrows-1 of one large Fletcher-Powell
+// request, tpr lanes per row; lane r of row i takes chunks c0 + r, c0 + r +
+// tpr, ... with c0 = floor(i/C) (SC-HESS-VEC, Alg. 8).  The trip count is the
+// tile's largest (the sweep's A/B tile loads are block-wide), lanes without a
+// chunk idle through the barriers.
+template <typename T, int C, int MB>
+__device__ __forceinline__ void ragged_sym_tile(const RaggedArgs &a, const RTile &t, const Job &job,
+                                                const ListPoints &pm, unsigned char *smem)
+{
+    __shared__ int s_last;
+    const int n = t.n, tpr = t.tpr;
+    const Smem<T> L = smem_layout<T>(FN_FP, true, n, t.maxpts, t.mt);
+    const long long p = t.row0 / n;
+    const int i0 = (int)(t.row0 - p * n);
+    point_prologue<T, T, FN_FP, true>(job, pm, smem, L, p, 1);
+    const int tid = threadIdx.x;
+    const int r = tid % tpr;
+    const bool active = tid / tpr < t.nrows;
+    const int i = active ? i0 + tid / tpr : i0;
+    const PointTables<T> pt(smem, L, 0, n);
+    const int q = a.list[t.list0 + p];
+    double *acc = a.acc + a.soffs[q];
+    const int c0 = i / C;
+    const int iters = (t.nch - i0 / C + tpr - 1) / tpr;
+    const double vi = (double)pt.v[i];
+    using Dot = typename std::conditional<IsComp<T>::value, CSum, T>::type;
+    Dot own;
+    if constexpr (IsComp<T>::value) {
+        own.s = 0.f;
+        own.e = 0.f;
+    } else {
+        own = T(0);
+    }
+    for (int it = 0; it < iters; ++it) {
+        const int j = c0 + r + it * tpr;
+        const bool has = active && j < t.nch;
+        const int cstart = j * C;
+        const HD<T, C> f = row_chunk<T, C, FN_FP, MB, true>(job, smem, L, pt, i, cstart, has, it == 0);
+        if (!has) continue;
+        const bool mirror = j > c0;
+#pragma unroll
+        for (int l = 0; l < C; ++l) {
+            const int jj = cstart + l;
+            if (jj < n) {
+                if constexpr (IsComp<T>::value) cdot_add(own, f.h[l], pt.v[jj]);
+                else own = fma_(f.h[l], pt.v[jj], own);
+                if (mirror) atomicAdd(&acc[jj], (double)f.h[l] * vi);  // H_ji v_i, H_ji = H_ij
+            }
+        }
+    }
+    // the row's lanes (aligned groups inside one warp), then one add per row
+    double rowsum;
+    if constexpr (IsComp<T>::value) {
+        for (int off = tpr >> 1; off > 0; off >>= 1) {
+            CSum o;
+            o.s = __shfl_xor_sync(0xffffffffu, own.s, off);
+            o.e = __shfl_xor_sync(0xffffffffu, own.e, off);
+            own = csum_merge(own, o);
+        }
+        rowsum = (double)own.s + (double)own.e;
+    } else {
+        for (int off = tpr >> 1; off > 0; off >>= 1) own += __shfl_xor_sync(0xffffffffu, own, off);
+        rowsum = (double)own;
+    }
+    if (active && r == 0) atomicAdd(&acc[i], rowsum);
+    // Publish this tile's adds, count its rows; the tile that completes the
+    // request rounds its accumulators into the output.
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = (atomicAdd(&a.done[q], t.nrows) + t.nrows == n);
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        T *O = reinterpret_cast<T *>(a.out) + pm.off(p);
+        for (int e = tid; e < n; e += blockDim.x) O[e] = (T)__ldcg(&acc[e]);
+    }
+}
 
 template <typename T, int C, int FN>
 __device__ __forceinline__ void ragged_tile(const RaggedArgs &a, const RTile &t, unsigned char *smem)
@@ -78,7 +174,9 @@ __device__ __forceinline__ void ragged_tile(const RaggedArgs &a, const RTile &t,
     job.mt = t.mt;
     job.ld = a.ld;
     ListPoints pm{a.list + t.list0, a.offs, a.eoffs, a.Epack};
-    if (IsComp<T>::value && t.n == 1) {
+    if (FN == FN_FP && t.sym) {
+        ragged_sym_tile<T, C, ragged_mb(C, sizeof(T) == 8)>(a, t, job, pm, smem);
+    } else if (IsComp<T>::value && t.n == 1) {
         // One variable: FP64 sweep with float I/O (the Hessian is a single
         // entry whose terms can cancel far below their size).
         block_sweeps<double, float, 1, FN, true, 8>(job, pm, smem);
@@ -119,10 +217,13 @@ struct chessfad_ragged_plan_s {
     size_t smem = 0;
     std::vector<RTile> tiles;
     std::vector<int> list;
-    std::vector<long long> offs, eoffs;
-    // device workspace layout (bytes)
-    size_t off_counter = 0, off_tiles = 0, off_list = 0, off_offs = 0, off_eoffs = 0, total = 0;
-    std::vector<unsigned char> image;  // host image of the workspace tables
+    std::vector<long long> offs, eoffs, soffs;
+    long long acc_elems = 0;  // FP64 accumulators of the symmetric requests
+    // device workspace layout (bytes): tables (uploaded), then the counter,
+    // the per-request row counters and the accumulators (zeroed every run)
+    size_t off_tiles = 0, off_list = 0, off_offs = 0, off_eoffs = 0, off_soffs = 0, off_counter = 0, off_done = 0,
+           off_acc = 0, table_bytes = 0, total = 0;
+    std::vector<unsigned char> image;  // host image of the tables (table_bytes)
     int grid_dev = -1, grid = 0;
     double est_cost = 0.0;
 };
@@ -179,7 +280,8 @@ cudaError_t launch_ragged(chessfad_ragged_plan_s *pl, const RaggedArgs &a, cudaS
         pl->grid_dev = dev;
     }
     if (a.ntiles == 0) return cudaSuccess;
-    e = cudaMemsetAsync(a.counter, 0, sizeof(int), stream);
+    // queue counter, per-request row counters and accumulators: contiguous
+    e = cudaMemsetAsync(a.counter, 0, pl->total - pl->off_counter, stream);
     if (e != cudaSuccess) return e;
     kern<<<std::min(pl->grid, a.ntiles), kRaggedBlock, pl->smem, stream>>>(a);
     return cudaGetLastError();
@@ -217,9 +319,14 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
     for (long long q = 0; q < nreq; ++q) groups[{reqs[q].fn, reqs[q].n}].push_back((int)q);
     pl->offs.resize(nreq);
     pl->eoffs.resize(nreq);
+    pl->soffs.assign(nreq, -1);
     for (long long q = 0; q < nreq; ++q) {
         pl->offs[q] = reqs[q].off;
         pl->eoffs[q] = reqs[q].fn == CHESSFAD_FLETCHER_POWELL ? reqs[q].eoff : 0;
+        if (reqs[q].fn == CHESSFAD_FLETCHER_POWELL && reqs[q].n >= kSymMinN) {
+            pl->soffs[q] = pl->acc_elems;
+            pl->acc_elems += reqs[q].n;
+        }
     }
     std::vector<std::pair<double, RTile>> work;
     size_t smem = 0;
@@ -243,6 +350,41 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
         smem = std::max(smem, bytes);
         const int list0 = (int)pl->list.size();
         for (int q : g.second) pl->list.push_back(q);
+        if (fn == CHESSFAD_FLETCHER_POWELL && n >= kSymMinN) {
+            // Symmetric tiles: rows of one point each; enough lanes per row
+            // that a tile's rows do not outnumber the point's.
+            int stpr = tpr;
+            while (stpr < 32 && kRaggedBlock / stpr > n) stpr *= 2;
+            const int srows = kRaggedBlock / stpr;
+            const int smt = fp_tile_rows_ragged(n, prec, mb);
+            const size_t sbytes = (prec == CHESSFAD_FP64) ? smem_layout<double>(fn, true, n, 1, smt).total
+                                                          : smem_layout<float>(fn, true, n, 1, smt).total;
+            smem = std::max(smem, sbytes);
+            const double sweep = sweep_cost(fn, n, C);
+            for (long long pt = 0; pt < np; ++pt) {
+                for (int i0 = 0; i0 < n; i0 += srows) {
+                    RTile t{};
+                    t.row0 = pt * n + i0;
+                    t.npoints = np;
+                    t.list0 = list0;
+                    t.fn = fn;
+                    t.n = n;
+                    t.nch = nch;
+                    t.tpr = stpr;
+                    t.maxpts = 1;
+                    t.mt = smt;
+                    t.sym = 1;
+                    t.nrows = std::min(srows, n - i0);
+                    // the block runs the longest row's chunk count (the rows
+                    // starting at i0 have the most chunks)
+                    const int iters = (nch - i0 / C + stpr - 1) / stpr;
+                    const double cost = (double)iters * stpr * t.nrows * sweep + 2000.0;
+                    work.push_back({cost, t});
+                    pl->est_cost += cost;
+                }
+            }
+            continue;
+        }
         const double per_row = nch * sweep_cost(fn, n, C);
         for (long long r0 = 0; r0 < total_rows; r0 += rows) {
             RTile t{};
@@ -255,6 +397,8 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
             t.tpr = tpr;
             t.maxpts = maxpts;
             t.mt = mt;
+            t.sym = 0;
+            t.nrows = rows;
             const double cost = per_row * (double)std::min<long long>(rows, total_rows - r0) + 2000.0;
             work.push_back({cost, t});
             pl->est_cost += cost;
@@ -266,19 +410,26 @@ int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, in
     for (auto &w : work) pl->tiles.push_back(w.second);
     pl->smem = smem;
 
-    // Workspace: counter | tiles | list | offs | eoffs.
-    pl->off_counter = 0;
-    pl->off_tiles = align256(sizeof(int));
+    // Workspace: tiles | list | offs | eoffs | soffs (the tables), then
+    // counter | done | acc (zeroed by every run).
+    pl->off_tiles = 0;
     pl->off_list = align256(pl->off_tiles + pl->tiles.size() * sizeof(RTile));
     pl->off_offs = align256(pl->off_list + pl->list.size() * sizeof(int));
     pl->off_eoffs = align256(pl->off_offs + pl->offs.size() * sizeof(long long));
-    pl->total = align256(pl->off_eoffs + pl->eoffs.size() * sizeof(long long));
-    pl->image.assign(pl->total, 0);
+    pl->off_soffs = align256(pl->off_eoffs + pl->eoffs.size() * sizeof(long long));
+    pl->table_bytes = align256(pl->off_soffs + pl->soffs.size() * sizeof(long long));
+    pl->off_counter = pl->table_bytes;
+    pl->off_done = align256(pl->off_counter + sizeof(int));
+    pl->off_acc = align256(pl->off_done + (size_t)nreq * sizeof(int));
+    pl->total = align256(pl->off_acc + (size_t)pl->acc_elems * sizeof(double));
+    pl->image.assign(pl->table_bytes, 0);
     if (!pl->tiles.empty()) std::memcpy(&pl->image[pl->off_tiles], pl->tiles.data(), pl->tiles.size() * sizeof(RTile));
     if (!pl->list.empty()) std::memcpy(&pl->image[pl->off_list], pl->list.data(), pl->list.size() * sizeof(int));
     if (!pl->offs.empty()) std::memcpy(&pl->image[pl->off_offs], pl->offs.data(), pl->offs.size() * sizeof(long long));
     if (!pl->eoffs.empty())
         std::memcpy(&pl->image[pl->off_eoffs], pl->eoffs.data(), pl->eoffs.size() * sizeof(long long));
+    if (!pl->soffs.empty())
+        std::memcpy(&pl->image[pl->off_soffs], pl->soffs.data(), pl->soffs.size() * sizeof(long long));
     *plan_out = pl;
     return CHESSFAD_SUCCESS;
 }
@@ -304,8 +455,8 @@ int chessfad_ragged_plan_upload(chessfad_ragged_plan plan, void *workspace, size
 {
     if (!plan) return CHESSFAD_ERR_PLAN;
     if (!workspace || workspace_bytes < plan->total) return CHESSFAD_ERR_WORKSPACE;
-    if (plan->total == 0) return CHESSFAD_SUCCESS;
-    cudaError_t e = cudaMemcpyAsync(workspace, plan->image.data(), plan->total, cudaMemcpyHostToDevice,
+    if (plan->table_bytes == 0) return CHESSFAD_SUCCESS;
+    cudaError_t e = cudaMemcpyAsync(workspace, plan->image.data(), plan->table_bytes, cudaMemcpyHostToDevice,
                                     (cudaStream_t)stream);
     return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
 }
@@ -335,7 +486,10 @@ int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpack, const void
     a.list = reinterpret_cast<const int *>(ws + plan->off_list);
     a.offs = reinterpret_cast<const long long *>(ws + plan->off_offs);
     a.eoffs = reinterpret_cast<const long long *>(ws + plan->off_eoffs);
+    a.soffs = reinterpret_cast<const long long *>(ws + plan->off_soffs);
     a.counter = reinterpret_cast<int *>(ws + plan->off_counter);
+    a.done = reinterpret_cast<int *>(ws + plan->off_done);
+    a.acc = reinterpret_cast<double *>(ws + plan->off_acc);
     a.ntiles = (int)plan->tiles.size();
     cudaError_t e;
     const cudaStream_t s = (cudaStream_t)stream;
@@ -405,8 +559,8 @@ extern "C" int chessfad_hvp_ragged_noalloc(chessfad_ragged_plan plan, const void
     int st = ragged_scratch_address(&scratch);
     if (st != CHESSFAD_SUCCESS) return st;
     const cudaStream_t s = (cudaStream_t)stream;
-    // The plan's image holds the tables and a zero queue counter.
-    if (cudaMemcpyAsync(scratch, plan->image.data(), plan->total, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // The plan's tables; the kernel launch zeroes the counters and accumulators.
+    if (cudaMemcpyAsync(scratch, plan->image.data(), plan->table_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
         return CHESSFAD_ERR_CUDA;
     unsigned char *ws = static_cast<unsigned char *>(scratch);
     RaggedArgs a{};
@@ -423,7 +577,10 @@ extern "C" int chessfad_hvp_ragged_noalloc(chessfad_ragged_plan plan, const void
     a.list = reinterpret_cast<const int *>(ws + plan->off_list);
     a.offs = reinterpret_cast<const long long *>(ws + plan->off_offs);
     a.eoffs = reinterpret_cast<const long long *>(ws + plan->off_eoffs);
+    a.soffs = reinterpret_cast<const long long *>(ws + plan->off_soffs);
     a.counter = reinterpret_cast<int *>(ws + plan->off_counter);
+    a.done = reinterpret_cast<int *>(ws + plan->off_done);
+    a.acc = reinterpret_cast<double *>(ws + plan->off_acc);
     a.ntiles = (int)plan->tiles.size();
     cudaError_t e;
     if (plan->prec == CHESSFAD_FP64)

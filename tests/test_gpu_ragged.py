@@ -121,3 +121,50 @@ def test_full_ragged_workload_sampled():
     idx = np.unique(np.concatenate([big, rnd]))
     e = d.errors(out, idx)
     assert e.max() <= BOUND[cf.FP32_COMP], (e.max(), np.median(e))
+
+
+def _ragged_from(fns, ns, seed, nmax=320):
+    """An uneven batch with the given functions and sizes (inputs drawn as in
+    the named workloads; A, B shared, E per Fletcher-Powell size)."""
+    base = W.make_ragged(nreq=1, seed=seed, nmax=nmax)
+    fns = np.asarray(fns, np.int32)
+    ns = np.asarray(ns, np.int32)
+    offs = np.zeros(len(ns), dtype=np.int64)
+    offs[1:] = np.cumsum(ns[:-1])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xp = np.concatenate([rng.uniform(*W.X_RANGE[int(f)], int(n)) for f, n in zip(fns, ns)])
+    vp = rng.uniform(-1, 1, int(ns.sum()))
+    Epack, e_of_n, pos = [], {}, 0
+    for n in sorted(set(int(n) for f, n in zip(fns, ns) if f == W.FLETCHER_POWELL)):
+        Epack.append(W.fp_rhs(base.fp.A[:n, :n], base.fp.B[:n, :n], base.fp.alpha[:n]))
+        e_of_n[n] = pos
+        pos += n
+    eoffs = np.array([e_of_n.get(int(n), 0) if f == W.FLETCHER_POWELL else 0 for f, n in zip(fns, ns)])
+    return W.Ragged(fns, ns, offs, xp, vp, base.fp, np.concatenate(Epack), eoffs, e_of_n)
+
+
+@pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
+@pytest.mark.parametrize("csize", [8, 16])
+def test_symmetric_fletcher_powell_requests(prec, csize):
+    """Fletcher-Powell requests with n >= 128 run SC-HESS-VEC (Alg. 8) with
+    FP64 accumulators shared across tiles: sizes on and off tile and chunk
+    boundaries, two requests of one size, mixed with small requests of every
+    function; every request against the oracle, on two runs."""
+    F, R, A = W.FLETCHER_POWELL, W.ROSENBROCK, W.ACKLEY
+    fns = [F, R, F, A, F, F, R, F, A, F]
+    ns = [128, 7, 131, 30, 200, 256, 300, 256, 150, 320]
+    rg = _ragged_from(fns, ns, seed=40 + csize)
+    d = DevRagged(rg, prec, csize)
+    first = d.run()
+    e = d.errors(first)
+    assert e.max() <= BOUND[prec], (e.max(), np.median(e))
+    d.out.fill_(float("nan"))
+    second = d.run()
+    assert hvp_close(first, second, prec)
+
+
+def hvp_close(a, b, prec):
+    # FP64 accumulation order may differ between runs (atomic adds)
+    if prec == cf.FP32_COMP:
+        return np.array_equal(a, b) or np.max(np.abs(a - b) / (1 + np.abs(a))) <= 1e-6
+    return np.max(np.abs(a - b) / (1 + np.abs(a))) <= 1e-13

@@ -75,12 +75,12 @@ def test_noalloc_matches_workspace_entry_point_on_two_calls(prec):
 
 
 def test_noalloc_rejects_tables_beyond_the_static_scratch():
-    # 600000 two-variable Rosenbrock requests need more table space than the
+    # 1500000 two-variable Rosenbrock requests need more table space than the
     # static scratch holds; the call is rejected before anything is launched.
-    n = 600000
+    n = 1500000
     reqs = cf.requests(np.zeros(n, np.int32), np.full(n, 2, np.int32), 2 * np.arange(n, dtype=np.int64))
     plan = cf.chessfad_ragged_plan_create(reqs, cf.FP32_COMP)
-    assert cf.chessfad_ragged_plan_info(plan)["workspace_bytes"] > 8 * 1024 * 1024
+    assert cf.chessfad_ragged_plan_info(plan)["workspace_bytes"] > 32 * 1024 * 1024
     dummy = ctypes.c_void_p(256).value
     assert cf.chessfad_hvp_ragged_noalloc(plan, dummy, dummy, dummy, None) == -8
     cf.chessfad_ragged_plan_destroy(plan)
