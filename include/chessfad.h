@@ -126,9 +126,12 @@ typedef struct {
  *                     (row, chunk) items, 32..256 power of two
  * Zero in any field means "default" (method 0 is the plain method).  The
  * symmetric HVP stages a point's chunks on and above the diagonal chunks in
- * shared memory (about n (n + C) / 2 values per point): it supports n up to
- * about 280 (FP32) / 200 (FP64) and returns CHESSFAD_ERR_SIZE beyond; the
- * symmetric Hessian has no such limit. */
+ * shared memory (about n (n + C) / 2 values per point) and sums whole rows,
+ * reproducibly, for n up to about 280 (FP32) / 200 (FP64); beyond, it sums
+ * each row in an FP64 shared-memory accumulator with atomic adds (the two
+ * updates of Alg. 8), whose order varies, so FP64 results of such sizes can
+ * differ from run to run in the last bits.  The symmetric Hessian writes
+ * chunks and their mirror images directly, at any n. */
 typedef struct {
     int csize;
     int threads_per_row;

@@ -175,7 +175,15 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         };
         int ppb = (int)std::min<long long>(batch, std::max(1, c.block_threads / c.threads_per_point));
         const size_t kBudget = 200 * 1024;
+        a.sym_acc = 0;
+        const int ppb0 = ppb;
         while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
+        if (hvp && bytes(ppb) > kBudget) {
+            // the chunk matrix of one point does not fit: FP64 row accumulators
+            a.sym_acc = 1;
+            ppb = ppb0;
+            while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
+        }
         if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
         a.maxpts = ppb;
         if (sparse) {
@@ -342,9 +350,9 @@ int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const v
         for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
             for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
         if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
-        for (int p : {32, 64, 128})
+        for (int p : {32, 64, 128, 256})
             for (int bt : {128, 256})
-                if (bt >= p) cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
+                if (bt >= p && (p < 256 || n >= 128)) cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
     }
     for (const chessfad_config &cfg : cands) {
         if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {

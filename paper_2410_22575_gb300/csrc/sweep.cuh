@@ -49,6 +49,7 @@ struct SweepArgs {
     int tpp;     // threads per point = n * tpr
     int maxpts;  // points staged per block (upper bound)
     int mt;      // Fletcher-Powell: rows of A, B per shared-memory tile
+    int sym_acc; // symmetric HVP: 0 = stage the chunk matrix, 1 = FP64 row accumulators
 };
 
 // Number of Ackley per-point scalars kept in the table.
@@ -849,6 +850,14 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
     const long long p = p0 + (active ? q : 0);
     const PointTables<T> pt(smem_raw, L, active ? q : 0, n);
     T *Hs = reinterpret_cast<T *>(smem_raw + align_up(L.total, 16) + (size_t)(active ? q : 0) * sym_hs_bytes<T>(n, C));
+    // Accumulator form of the HVP (points whose chunk matrix does not fit
+    // shared memory): one FP64 accumulator per row of each staged point.
+    double *accs = reinterpret_cast<double *>(smem_raw + align_up(L.total, 16)) + (size_t)(active ? q : 0) * n;
+    const bool acc_form = HVP && a.sym_acc;
+    if (acc_form) {
+        for (int e = tid; e < npts * n; e += blockDim.x) reinterpret_cast<double *>(smem_raw + align_up(L.total, 16))[e] = 0.0;
+        __syncthreads();
+    }
 
     const int nch = a.nch;
     const int items = C * nch * (nch + 1) / 2;
@@ -866,10 +875,28 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
         const HD<T, C> f = row_chunk<T, C, FN, MB, true, kSparse>(job, smem_raw, L, pt, i, cstart, has, it == 0);
         if (!has) continue;
         if constexpr (HVP) {
-            T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
+            if (acc_form) {
+                // r_i += sum_l H_il v_l; off the diagonal chunk also r_l += H_il v_i
+                // (Alg. 8's two updates), into FP64 (products of two FP32 values
+                // are exact there)
+                const bool mirror = cn > i / C;
+                const double vi = (double)pt.v[i];
+                double own = 0.0;
 #pragma unroll
-            for (int l = 0; l < C; ++l)
-                if (cstart + l < n) hrow[cstart + l] = f.h[l];
+                for (int l = 0; l < C; ++l) {
+                    const int j = cstart + l;
+                    if (j < n) {
+                        own = fma((double)f.h[l], (double)pt.v[j], own);
+                        if (mirror) atomicAdd(&accs[j], (double)f.h[l] * vi);
+                    }
+                }
+                atomicAdd(&accs[i], own);
+            } else {
+                T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
+#pragma unroll
+                for (int l = 0; l < C; ++l)
+                    if (cstart + l < n) hrow[cstart + l] = f.h[l];
+            }
         } else {
             IO *H = reinterpret_cast<IO *>(a.out) + (size_t)p * n * n;
             const bool mirror = cn > i / C;
@@ -890,7 +917,10 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
         // (H_sj = H_js), so every off-diagonal-chunk entry serves both r_i and
         // r_s as in Alg. 8.
         __syncthreads();
-        if (active) {
+        if (active && acc_form) {
+            IO *O = reinterpret_cast<IO *>(a.out) + (size_t)p * n;
+            for (int srow = t; srow < n; srow += tpp) O[srow] = (IO)accs[srow];
+        } else if (active) {
             const T *Hq = Hs;
             IO *O = reinterpret_cast<IO *>(a.out) + (size_t)p * n;
             for (int srow = t; srow < n; srow += tpp) {
@@ -948,6 +978,7 @@ template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 size_t sym_smem_bytes(const SweepArgs &a)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
+    if (HVP && a.sym_acc) return align_up(L.total, 16) + (size_t)a.maxpts * a.n * sizeof(double);
     return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n, C) : 0);
 }
 

@@ -169,17 +169,31 @@ def test_symmetric_sizes(fn, prec, n):
 
 
 def test_symmetric_limits():
-    import torch
-
-    # symmetric Hessian at n = 300 (no staging limit); symmetric HVP beyond
-    # the shared-memory limit is rejected with CHESSFAD_ERR_SIZE
+    # symmetric Hessian at n = 300 (no staging); symmetric HVP beyond the
+    # staging limit (FP64 n > ~200, FP32 n > ~280) sums rows in FP64
+    # shared-memory accumulators
     d = Dev(W.make_batch(W.ROSENBROCK, 300, 2, seed=1), cf.FP64)
     cfg = cf.Config(16, 0, 0, cf.SYMMETRIC, 128)
     assert hessian_err(d, d.hessian(cfg=cfg)).max() <= BOUND[cf.FP64]
-    out = torch.empty_like(d.x)
-    assert cf.chessfad_hvp_config(W.ROSENBROCK, 300, 2, cfg, d.x, d.v, out, None, cf.FP64) == -2
+    assert hvp_err(d, d.hvp(cfg=cfg)).max() <= BOUND[cf.FP64]
     d32 = Dev(W.make_batch(W.ACKLEY, 200, 3, seed=2), cf.FP32_COMP)
     assert hvp_err(d32, d32.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC, 64))).max() <= BOUND[cf.FP32_COMP]
+
+
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+def test_symmetric_hvp_accumulator_form(fn, prec):
+    """n = 512 and 300: the chunk matrix of a point exceeds shared memory, the
+    symmetric HVP accumulates rows in FP64 (both updates of Alg. 8)."""
+    for n, batch in ((300, 5), (512, 3)):
+        if fn == W.FLETCHER_POWELL and n == 512:
+            batch = 2
+        d = Dev(W.make_batch(fn, n, batch, seed=60 + n), prec)
+        for c, tpp in ((8, 64), (16, 128)):
+            e = hvp_err(d, d.hvp(cfg=cf.Config(c, 0, 0, cf.SYMMETRIC, tpp)))
+            assert e.max() <= BOUND[prec], (n, c, e.max())
+        e = hvp_err(d, d.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC_SPARSE, 64)))
+        assert e.max() <= BOUND[prec], (n, "sparse", e.max())
 
 
 def test_symmetric_deterministic_and_equal_to_plain_within_bound():
