@@ -344,8 +344,9 @@ CHESSFAD_API int chessfad_version(void);
  * the row's ceil(n/csize) chunks) and symmetric (SC-HESS-VEC, Alg. 8 /
  * SCHUNK-HESS, Alg. 6: threads_per_point threads share a point's (row, chunk
  * >= diagonal chunk) items; the HVP stages a point's chunks in shared memory,
- * which bounds n at about 280 (FP32) / 200 (FP64)).  x, v, out, H as for
- * chessfad_hvp / chessfad_hessian, 1 <= n <= CHESSFAD_MAX_N.
+ * or, where they do not fit, sums rows in FP64 shared-memory accumulators
+ * with atomic adds, reproducible to the last FP64 bits only).  x, v, out, H
+ * as for chessfad_hvp / chessfad_hessian, 1 <= n <= CHESSFAD_MAX_N.
  * --------------------------------------------------------------------------- */
 typedef struct chessfad_user_fn chessfad_user_fn;
 
@@ -370,9 +371,8 @@ CHESSFAD_API int chessfad_user_fn_info(const chessfad_user_fn *fn, int hvp, int 
                                        int *local_bytes);
 
 /* out[p] = H(x_p) v_p for the user's f, p < batch; types by the handle's
- * precision (double, or float for CHESSFAD_FP32_COMP).  The symmetric method
- * (32 threads per point) when its staging fits shared memory, else the plain
- * one.  Asynchronous on `stream`; allocates nothing.  The first symmetric
+ * precision (double, or float for CHESSFAD_FP32_COMP), by the symmetric
+ * method with 32 threads per point.  Asynchronous on `stream`; allocates nothing.  The first symmetric
  * launch on a device that needs more than 48 KiB of shared memory raises the
  * kernel's limit (a host call; make it before capturing a CUDA graph). */
 CHESSFAD_API int chessfad_user_hvp(chessfad_user_fn *fn, int n, long long batch, const void *x, const void *v,
@@ -389,8 +389,7 @@ CHESSFAD_API int chessfad_user_hessian(chessfad_user_fn *fn, int n, long long ba
  * handle's (else CHESSFAD_ERR_CHUNK); method CHESSFAD_METHOD_PLAIN or
  * _SYMMETRIC (else CHESSFAD_ERR_CONFIG); threads_per_row 0 or 1;
  * block_threads 0 (= 256) or 32..256, a multiple of 32; threads_per_point 0
- * (= 32) or 32..256, a power of two.  A symmetric HVP whose staging does not
- * fit shared memory returns CHESSFAD_ERR_SIZE. */
+ * (= 32) or 32..256, a power of two. */
 CHESSFAD_API int chessfad_user_hvp_config(chessfad_user_fn *fn, int n, long long batch, const chessfad_config *cfg,
                                           const void *x, const void *v, void *out, const double *params,
                                           chessfad_stream_t stream);

@@ -118,6 +118,7 @@ struct UserArgs {  // the kernels' chessfad::user::UserArgs, field for field
     int n;
     int maxpts;
     int tpp;
+    int acc;
 };
 
 long long hs_elems(int n, int C)  // staged chunk matrix of one point, symmetric HVP
@@ -129,12 +130,13 @@ long long hs_elems(int n, int C)  // staged chunk matrix of one point, symmetric
 // Resolve a launch configuration for a handle: method 0 = plain, 1 =
 // symmetric; -1 = symmetric when its shared memory fits, else plain.
 int resolve(const chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, int n, long long batch, int &method,
-            int &bt, int &tpp, int &ppb, size_t &smem)
+            int &bt, int &tpp, int &ppb, size_t &smem, int &acc)
 {
     const size_t elem = fn->prec == CHESSFAD_FP64 ? sizeof(double) : sizeof(float);
     method = -1;
     bt = 0;
     tpp = 0;
+    acc = 0;
     if (cfg) {
         if (cfg->csize != 0 && cfg->csize != fn->csize) return CHESSFAD_ERR_CHUNK;
         if (cfg->method != CHESSFAD_METHOD_PLAIN && cfg->method != CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_CONFIG;
@@ -151,15 +153,20 @@ int resolve(const chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, in
     if (tpp == 0) tpp = 32;
     if (method != CHESSFAD_METHOD_PLAIN) {
         if (tpp > bt) bt = tpp;
-        const size_t per_pt = ((size_t)n * (hvp ? 2 : 1) + (hvp ? (size_t)hs_elems(n, fn->csize) : 0)) * elem;
-        long long p = bt / tpp;
-        if (p > batch) p = batch;
-        while (p > 1 && (size_t)p * per_pt > kSmemBudget) --p;
-        if ((size_t)p * per_pt <= kSmemBudget) {
-            method = CHESSFAD_METHOD_SYMMETRIC;
-            ppb = (int)p;
-            smem = (size_t)p * per_pt;
-            return CHESSFAD_SUCCESS;
+        // staged chunk matrix, else (HVP) FP64 row accumulators
+        for (int form = 0; form < (hvp ? 2 : 1); ++form) {
+            const size_t per_pt = form == 0 ? ((size_t)n * (hvp ? 2 : 1) + (hvp ? (size_t)hs_elems(n, fn->csize) : 0)) * elem
+                                            : (size_t)n * 2 * elem + (size_t)n * sizeof(double);
+            long long p = bt / tpp;
+            if (p > batch) p = batch;
+            while (p > 1 && (size_t)p * per_pt > kSmemBudget) --p;
+            if ((size_t)p * per_pt <= kSmemBudget) {
+                method = CHESSFAD_METHOD_SYMMETRIC;
+                ppb = (int)p;
+                smem = (size_t)p * per_pt;
+                acc = form;
+                return CHESSFAD_SUCCESS;
+            }
         }
         if (method == CHESSFAD_METHOD_SYMMETRIC) return CHESSFAD_ERR_SIZE;
     }
@@ -176,13 +183,13 @@ int launch(chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, int n, lo
     if (!fn || !fn->lib) return CHESSFAD_ERR_NULL;
     if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
     if (batch < 0) return CHESSFAD_ERR_BATCH;
-    int method, bt, tpp, ppb = 0;
+    int method, bt, tpp, ppb = 0, acc = 0;
     size_t smem = 0;
-    int st = resolve(fn, cfg, hvp, n, batch > 0 ? batch : 1, method, bt, tpp, ppb, smem);
+    int st = resolve(fn, cfg, hvp, n, batch > 0 ? batch : 1, method, bt, tpp, ppb, smem, acc);
     if (st != CHESSFAD_SUCCESS) return st;
     if (batch == 0) return CHESSFAD_SUCCESS;
     if (!x || !out || (hvp && !v)) return CHESSFAD_ERR_NULL;
-    UserArgs args{x, hvp ? v : x, out, batch, params, n, ppb, tpp};
+    UserArgs args{x, hvp ? v : x, out, batch, params, n, ppb, tpp, acc};
     long long grid;
     unsigned block;
     cudaKernel_t k;

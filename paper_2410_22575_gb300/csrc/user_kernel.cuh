@@ -37,6 +37,7 @@ struct UserArgs {
     int maxpts;  // plain: points staged per CTA, min(batch, (blockDim - 1) / n + 2);
                  // symmetric: points per CTA
     int tpp;     // symmetric: threads per point
+    int acc;     // symmetric HVP: 0 = stage the chunk matrix, 1 = FP64 row accumulators
 };
 
 template <typename T>
@@ -105,7 +106,10 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, ppb = a.maxpts, tpp = a.tpp;
-    T *xs = reinterpret_cast<T *>(smem_raw);
+    // accumulators first (8-byte aligned), then x, v and the staged chunks
+    double *accs = reinterpret_cast<double *>(smem_raw);
+    const bool acc_form = HVP && a.acc;
+    T *xs = reinterpret_cast<T *>(smem_raw + (acc_form ? (size_t)ppb * n * sizeof(double) : 0));
     T *vs = xs + (size_t)ppb * n;
     T *hs = vs + (HVP ? (size_t)ppb * n : 0);
     const long long p0 = (long long)blockIdx.x * ppb;
@@ -115,9 +119,11 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
     for (int e = threadIdx.x; e < npts * n; e += blockDim.x) {
         xs[e] = xg[e];
         if (HVP) vs[e] = vg[e];
+        if (acc_form) accs[e] = 0.0;
     }
     __syncthreads();
     const int q = threadIdx.x / tpp, t = threadIdx.x - q * tpp;
+    double *acc = accs + (size_t)q * n;
     const bool active = q < npts;
     const long long p = p0 + q;
     const T *xp = xs + (size_t)q * n;
@@ -132,7 +138,22 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
         const int cstart = cn * C;
         const Vars<T, C> x{xp, i, cstart, z};
         const Num<T, C> r = ::CHESSFAD_USER_FN<Num<T, C>, Vars<T, C>>(x, n, a.params);
-        if (HVP) {
+        if (HVP && acc_form) {
+            // r_i += sum_l H_il v_l; off the diagonal chunk also r_l += H_il v_i
+            const T *vp = vs + (size_t)q * n;
+            const bool mirror = cn > i / C;
+            const double vi = (double)vp[i];
+            double own = 0.0;
+#pragma unroll
+            for (int l = 0; l < C; ++l) {
+                const int j = cstart + l;
+                if (j < n) {
+                    own = fma((double)r.a.h[l], (double)vp[j], own);
+                    if (mirror) atomicAdd(&acc[j], (double)r.a.h[l] * vi);
+                }
+            }
+            atomicAdd(&acc[i], own);
+        } else if (HVP) {
             T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
 #pragma unroll
             for (int l = 0; l < C; ++l)
@@ -154,7 +175,10 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
         // r_s = sum_j H_sj v_j: entries right of row s's diagonal chunk from
         // row s, entries left of it from column s (H_sj = H_js).
         __syncthreads();
-        if (active) {
+        if (active && acc_form) {
+            T *O = static_cast<T *>(a.out) + p * n;
+            for (int srow = t; srow < n; srow += tpp) O[srow] = (T)acc[srow];
+        } else if (active) {
             const T *vp = vs + (size_t)q * n;
             T *O = static_cast<T *>(a.out) + p * n;
             for (int srow = t; srow < n; srow += tpp) {

@@ -154,10 +154,12 @@ def test_user_symmetric_limits_and_config_errors():
     f = user_fn(W.ROSENBROCK, 8, cf.FP64)
     k = Case(W.ROSENBROCK, 300, 3, 17, cf.FP64)
     out = torch.empty_like(k.x)
-    # the symmetric HVP's staging does not fit: explicit request rejected,
-    # the default falls back to the plain method
-    assert cf.chessfad_user_hvp_config(f.handle, 300, 3, SYM, k.x, k.v, out) == -2
+    # the symmetric HVP's chunk matrix does not fit shared memory: FP64 row
+    # accumulators instead, explicitly and by default
+    assert k.hvp_err(f.hvp(k.x, k.v, cfg=SYM)).max() <= 1e-12
     assert k.hvp_err(f.hvp(k.x, k.v)).max() <= 1e-12
+    k32 = Case(W.MIX, 512, 3, 18, cf.FP32_COMP)
+    assert k32.hvp_err(user_fn(W.MIX, 16, cf.FP32_COMP).hvp(k32.x, k32.v, cfg=SYM)).max() <= 1e-5
     # the symmetric Hessian has no staging limit
     assert k.hess_err(f.hessian(k.x, cfg=SYM)).max() <= 1e-12
     for bad, code in ((cf.Config(4, 0, 0, cf.PLAIN, 0), -4), (cf.Config(0, 0, 0, cf.SYMMETRIC_SPARSE, 0), -9),
