@@ -123,7 +123,8 @@ typedef struct {
  *                     one; fewer when the staged chunks of an HVP do not fit
  *                     shared memory)
  *   threads_per_point symmetric method: threads sharing one point's
- *                     (row, chunk) items, 32..256 power of two
+ *                     (row, chunk) items, 8..256 power of two (below 32 a
+ *                     warp serves several points)
  * Zero in any field means "default" (method 0 is the plain method).  The
  * symmetric HVP stages a point's chunks on and above the diagonal chunks in
  * shared memory (about n (n + C) / 2 values per point) and sums whole rows,

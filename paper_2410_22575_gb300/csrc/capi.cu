@@ -112,7 +112,7 @@ static int check_config(const chessfad_config &c)
     if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE && c.csize != 4 && c.csize != 8 && c.csize != 16)
         return CHESSFAD_ERR_CHUNK;
     const int p = c.threads_per_point;
-    if (p < 32 || p > 256 || (p & (p - 1))) return CHESSFAD_ERR_CONFIG;
+    if (p < 8 || p > 256 || (p & (p - 1))) return CHESSFAD_ERR_CONFIG;
     return CHESSFAD_SUCCESS;
 }
 
@@ -350,9 +350,11 @@ int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const v
         for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
             for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
         if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
-        for (int p : {32, 64, 128, 256})
+        // threads per point: 8 for small n (few items per point), 256 for large n
+        for (int p : {8, 16, 32, 64, 128, 256})
             for (int bt : {128, 256})
-                if (bt >= p && (p < 256 || n >= 128)) cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
+                if (bt >= p && (p < 256 || n >= 128) && (p > 8 || n <= 32))
+                    cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
     }
     for (const chessfad_config &cfg : cands) {
         if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {

@@ -70,7 +70,7 @@ def test_argument_errors_without_gpu():
     for c in (1, 2, 32):  # seed-sparse kernels: chunk sizes 4, 8 and 16 only
         bad = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, 32)
         assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
-    for tpp in (16, 48, 512):
+    for tpp in (4, 48, 512):
         bad = cf.Config(4, 0, 0, cf.SYMMETRIC, tpp)
         assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
 

@@ -148,7 +148,7 @@ def test_symmetric_every_chunk(fn, prec, c):
     """SC-HESS-VEC (Alg. 8) and SCHUNK-HESS (Alg. 6) against the oracle, n = 19
     (ragged last chunk and last chunk row)."""
     d = Dev(W.make_batch(fn, 19, 75, seed=300 + c), prec)
-    for tpp in (32, 64):
+    for tpp in (8, 16, 32, 64):
         cfg = cf.Config(c, 0, 0, cf.SYMMETRIC, tpp)
         e = hvp_err(d, d.hvp(cfg=cfg))
         assert e.max() <= BOUND[prec], (tpp, e.max())
