@@ -91,7 +91,7 @@ def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
 
 # Sources that define the headline sweep kernel (the ncu traffic figure is
 # reported only while these are unchanged since the capture).
-KERNEL_SOURCES = ("hdual.cuh", "sweep.cuh", "dispatch.h", "k_ackley_f32c.cu")
+KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "k_ackley_f32c.cu")
 
 
 def kernel_source_hash() -> str:
