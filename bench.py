@@ -588,6 +588,43 @@ def kernel_only(args):
                       **cfg.as_dict(), "ms": ms, "hvp_per_s": b.batch / (min(ms) * 1e-3)}))
 
 
+def ragged_only(args):
+    """Run only the uneven-batch kernel on a subset of the 100000-request
+    workload (the requests of one function with n in [--ragged-min-n,
+    --ragged-max-n], the first --ragged-count of them): W + K launches, the
+    command the ncu summary of the persistent kernel captures."""
+    import numpy as np
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    rg = W.make_ragged()
+    idx = np.nonzero((rg.fns == args.ragged_fn) & (rg.ns >= args.ragged_min_n) & (rg.ns <= args.ragged_max_n))[0]
+    sub = rg.subset(idx[: args.ragged_count])
+    prec = cf.FP64 if args.prec == "fp64" else cf.FP32_COMP
+    dt = torch.float64 if prec == cf.FP64 else torch.float32
+    plan = cf.RaggedPlan(cf.requests(sub.fns, sub.ns, sub.offs, sub.eoffs), prec, args.csize)
+    x = torch.tensor(sub.xpack, dtype=dt, device="cuda")
+    v = torch.tensor(sub.vpack, dtype=dt, device="cuda")
+    out = torch.empty_like(x)
+    keep = [torch.tensor(a, device="cuda") for a in (sub.fp.A, sub.fp.B, sub.Epack)]
+    params = cf.fp_params(*keep)
+    ms = []
+    for k in range(args.warmup + args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.run(x, v, out, params)
+        e1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"mode": "ragged-only", "requests": len(sub.fns), "fn": args.ragged_fn,
+                      "n_range": [int(sub.ns.min()), int(sub.ns.max())], "prec": args.prec, "csize": args.csize, "plan": plan.info,
+                      "ms": ms, "hvp_per_s": len(sub.fns) / (min(ms) * 1e-3)}))
+
+
 def report(args):
     """Per-workload table for the benchmark spec: HVP/s (and Hessians/s) for every
     named workload in both precisions, autotuned over both methods, plus the
@@ -755,6 +792,12 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the 100000-request uneven batch")
     ap.add_argument("--ragged-steps", type=int, default=1)
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
+    ap.add_argument("--ragged-only", action="store_true",
+                    help="run only the uneven-batch kernel on a subset of the 100000-request workload (for ncu)")
+    ap.add_argument("--ragged-fn", type=int, default=2)
+    ap.add_argument("--ragged-min-n", type=int, default=256)
+    ap.add_argument("--ragged-max-n", type=int, default=512)
+    ap.add_argument("--ragged-count", type=int, default=32)
     ap.add_argument("--report", action="store_true", help="per-workload table (all named workloads)")
     ap.add_argument("--chunk-study", action="store_true", help="measured best chunk size vs the Sec. V model")
     ap.add_argument("--cpu-report", action="store_true", help="CPU-baseline leg for every named workload")
@@ -782,6 +825,8 @@ def main():
         report(args)
     elif args.kernel_only:
         kernel_only(args)
+    elif args.ragged_only:
+        ragged_only(args)
     elif args.impl == "reference":
         reference_arm(args)
     else:
