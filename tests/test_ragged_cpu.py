@@ -51,3 +51,41 @@ def test_plan_tiles_cover_the_uneven_batch():
     assert info["ntiles"] >= sum(-(-cnt * n // 256) for (f, n), cnt in groups.items())
     assert info["smem_bytes"] <= 227 * 1024
     cf.chessfad_ragged_plan_destroy(h)
+
+
+def _sym_rows(n, csize):
+    """Rows per symmetric tile: lanes per row doubled from the plain choice
+    until a tile holds no more rows than the request has."""
+    nch = -(-n // csize)
+    tpr = 1
+    while tpr * 2 <= max(1, nch // 8):
+        tpr *= 2
+    tpr = min(32, tpr)
+    while tpr < 32 and 256 // tpr > n:
+        tpr *= 2
+    return 256 // tpr
+
+
+@pytest.mark.parametrize("csize", [8, 16])
+def test_symmetric_tiles_and_accumulator_workspace(csize):
+    """Fletcher-Powell requests with n >= 128 get tiles of one point each
+    (ceil(n / rows) of them) and n FP64 accumulators plus a row counter in the
+    workspace; smaller requests and other functions keep the plain tiling."""
+    big = [(2, 128), (2, 200), (2, 512), (2, 300)]
+    fns = [f for f, _ in big]
+    ns = [n for _, n in big]
+    offs = np.concatenate([[0], np.cumsum(ns[:-1])])
+    h = cf.chessfad_ragged_plan_create(cf.requests(fns, ns, offs, [0] * len(ns)), cf.FP32_COMP, csize)
+    info = cf.chessfad_ragged_plan_info(h)
+    assert info["ntiles"] == sum(-(-n // _sym_rows(n, csize)) for n in ns)
+    assert info["workspace_bytes"] >= 8 * sum(ns) + 4 * len(ns)
+    cf.chessfad_ragged_plan_destroy(h)
+    # the same sizes as Rosenbrock requests: plain tiles, no accumulators
+    h2 = cf.chessfad_ragged_plan_create(cf.requests([0] * len(ns), ns, offs), cf.FP32_COMP, csize)
+    info2 = cf.chessfad_ragged_plan_info(h2)
+    assert info2["workspace_bytes"] < info["workspace_bytes"]
+    cf.chessfad_ragged_plan_destroy(h2)
+    # one request below the threshold: plain tiling of a 127-variable request
+    h3 = cf.chessfad_ragged_plan_create(cf.requests([2], [127], [0], [0]), cf.FP32_COMP, csize)
+    assert cf.chessfad_ragged_plan_info(h3)["ntiles"] == 1
+    cf.chessfad_ragged_plan_destroy(h3)
