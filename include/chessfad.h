@@ -109,6 +109,12 @@ typedef struct {
                                        the dense one for finite inputs, but NaN/Inf in the skipped
                                        variables does not reach the derivatives.  csize 4, 8 or 16;
                                        never chosen by the autotuner. */
+#define CHESSFAD_METHOD_POINT 3     /* the L0 decomposition (L0-HESS-VEC, Alg. 9): one thread per
+                                       point sweeps every chunk of every row (CHESS-VEC, Alg. 7 /
+                                       CHUNK-HESS, Alg. 5); block_threads points per CTA; csize
+                                       1..16; the same arithmetic, in the same order per row, as
+                                       the plain method with one thread per row, so the results
+                                       are identical.  Never chosen by the autotuner. */
 
 /* Launch configuration of the (point, row, chunk) decomposition.
  *   csize             chunk size, 1..32 power of two
@@ -116,7 +122,7 @@ typedef struct {
  *                     two, 1..32); lane r of a row evaluates chunks r, r+tpr,
  *                     ... and the row sum is finished by warp shuffles
  *                     (Sec. VI, Fig. 2 does this through shared memory)
- *   method            CHESSFAD_METHOD_PLAIN, _SYMMETRIC or _SYMMETRIC_SPARSE
+ *   method            CHESSFAD_METHOD_PLAIN, _SYMMETRIC, _SYMMETRIC_SPARSE or _POINT
  *   block_threads     plain method: CTA size, multiple of 32, 32..256;
  *                     symmetric method: the CTA holds
  *                     block_threads / threads_per_point points (at least

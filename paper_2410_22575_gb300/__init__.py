@@ -42,7 +42,7 @@ class FPParams(ctypes.Structure):
     _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("E", ctypes.c_void_p), ("ld", ctypes.c_int)]
 
 
-PLAIN, SYMMETRIC, SYMMETRIC_SPARSE = 0, 1, 2
+PLAIN, SYMMETRIC, SYMMETRIC_SPARSE, POINT = 0, 1, 2, 3
 
 
 class Config(ctypes.Structure):
@@ -53,7 +53,8 @@ class Config(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {"csize": self.csize, "threads_per_row": self.threads_per_row, "block_threads": self.block_threads,
-                "method": {PLAIN: "plain", SYMMETRIC: "symmetric", SYMMETRIC_SPARSE: "symmetric_sparse"}.get(
+                "method": {PLAIN: "plain", SYMMETRIC: "symmetric", SYMMETRIC_SPARSE: "symmetric_sparse",
+                           POINT: "point"}.get(
                     self.method, str(self.method)),
                 "threads_per_point": self.threads_per_point}
 

@@ -12,6 +12,7 @@
 
 #include "../../include/chessfad.h"
 #include "dispatch.h"
+#include "point.h"
 
 namespace chessfad {
 
@@ -75,8 +76,10 @@ static chessfad_config resolve(int fn, int n, long long batch, int prec, const c
         if (c.threads_per_point == 0) c.threads_per_point = base.threads_per_point;
         if (!cfg || cfg->method == 0) c.method = base.method;
         c.csize = base.csize;
-        // the seed-sparse kernels exist for chunk sizes 4, 8 and 16 only
+        // the seed-sparse kernels exist for chunk sizes 4, 8 and 16 only, the
+        // one-thread-per-point kernels for 1 .. 16
         if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE) c.csize = std::min(16, std::max(4, c.csize));
+        if (c.method == CHESSFAD_METHOD_POINT) c.csize = std::min(16, c.csize);
     }
     if (c.threads_per_point == 0) c.threads_per_point = default_threads_per_point(n, batch);
     if (c.threads_per_row == 0 || c.block_threads == 0) {
@@ -107,10 +110,11 @@ static int check_config(const chessfad_config &c)
     if (t < 1 || t > 32 || (t & (t - 1))) return CHESSFAD_ERR_CONFIG;
     if (c.block_threads < 32 || c.block_threads > 256 || c.block_threads % 32) return CHESSFAD_ERR_CONFIG;
     if (c.method != CHESSFAD_METHOD_PLAIN && c.method != CHESSFAD_METHOD_SYMMETRIC &&
-        c.method != CHESSFAD_METHOD_SYMMETRIC_SPARSE)
+        c.method != CHESSFAD_METHOD_SYMMETRIC_SPARSE && c.method != CHESSFAD_METHOD_POINT)
         return CHESSFAD_ERR_CONFIG;
     if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE && c.csize != 4 && c.csize != 8 && c.csize != 16)
         return CHESSFAD_ERR_CHUNK;
+    if (c.method == CHESSFAD_METHOD_POINT && c.csize > 16) return CHESSFAD_ERR_CHUNK;
     const int p = c.threads_per_point;
     if (p < 8 || p > 256 || (p & (p - 1))) return CHESSFAD_ERR_CONFIG;
     return CHESSFAD_SUCCESS;
@@ -213,6 +217,22 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
                 break;
             }
         }
+        return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
+    }
+    if (c.method == CHESSFAD_METHOD_POINT && !(!f64 && n == 1)) {
+        // L0 (Alg. 9): one thread per point; as many points per CTA as the CTA
+        // size allows within 200 KiB of shared memory, at least 32.
+        a.tpr = 1;
+        a.tpp = 1;
+        auto bytes = [&](int ppb) {
+            a.maxpts = ppb;
+            return f64 ? smem_point_f64(fn, c.csize, hvp, a) : smem_point_f32c(fn, c.csize, hvp, a);
+        };
+        int ppb = c.block_threads;
+        while (ppb > 32 && bytes(ppb) > 200 * 1024) ppb -= 32;
+        if (bytes(ppb) > 200 * 1024) return CHESSFAD_ERR_SIZE;
+        a.maxpts = ppb;
+        e = f64 ? launch_point_f64(fn, c.csize, hvp, a, stream) : launch_point_f32c(fn, c.csize, hvp, a, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }
     if (!f64 && n == 1) {

@@ -65,8 +65,10 @@ def test_argument_errors_without_gpu():
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
     bad = cf.Config(5, 4, 256)
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
-    bad = cf.Config(4, 0, 0, 3, 0)  # unknown method
+    bad = cf.Config(4, 0, 0, 4, 0)  # unknown method
     assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -9
+    bad = cf.Config(32, 0, 0, cf.POINT, 0)  # one-thread-per-point kernels: chunk sizes 1..16
+    assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4
     for c in (1, 2, 32):  # seed-sparse kernels: chunk sizes 4, 8 and 16 only
         bad = cf.Config(c, 0, 0, cf.SYMMETRIC_SPARSE, 32)
         assert lib.chessfad_hvp_config(0, 8, 4, ctypes.byref(bad), dummy, dummy, dummy, None, 0, None) == -4

@@ -263,3 +263,26 @@ def test_symmetric_sparse_chunk_auto_and_nan_point():
     assert np.all(np.isfinite(out[ok]))
     e = hvp_err(d, out)
     assert e[ok].max() <= BOUND[cf.FP64]
+
+
+# ------------------------------------------------------------------ L0 / L1 / L2
+@pytest.mark.parametrize("fn", FNS)
+@pytest.mark.parametrize("prec", PRECS)
+def test_decompositions_l0_l1_l2(fn, prec):
+    """The paper's three GPU decompositions (Sec. VI) compute the same HVP:
+    L0 (one thread per point, Alg. 9) and L1 (one thread per row, Alg. 10)
+    evaluate the same chunks in the same order per row, so their results are
+    identical; L2 (a row's chunks over lanes, Fig. 2) sums in another order and
+    agrees within the bound.  n = 21: ragged last chunk; 300 points: several
+    CTAs and a partial one."""
+    d = Dev(W.make_batch(fn, 21, 300, seed=70), prec)
+    for c in (1, 4, 8, 16):
+        nch = -(-21 // c)
+        l0 = d.hvp(cfg=cf.Config(c, 0, 64, cf.POINT, 0))
+        l1 = d.hvp(cfg=cf.Config(c, 1, 256))
+        l2 = d.hvp(cfg=cf.Config(c, min(32, 1 << (nch - 1).bit_length()), 256))
+        assert np.array_equal(l0, l1), c
+        assert hvp_err(d, l0).max() <= BOUND[prec], c
+        assert hvp_err(d, l2).max() <= BOUND[prec], c
+        H0 = d.hessian(cfg=cf.Config(c, 0, 32, cf.POINT, 0))
+        assert hessian_err(d, H0).max() <= BOUND[prec], c
