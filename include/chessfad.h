@@ -207,9 +207,10 @@ CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int pre
  * candidates on the caller's buffers (x, v, out as for chessfad_hvp; out is
  * overwritten): for every chunk size (largest first, following the Sec. V
  * operation-count model) the plain method over (threads_per_row,
- * block_threads) and the symmetric method over threads_per_point, discarding
- * kernels that spill registers and symmetric HVPs that do not fit shared
- * memory.  The winner is stored in the process-wide table used by
+ * block_threads) and the symmetric method over (threads_per_point 8..256,
+ * block_threads), discarding chunk sizes whose kernels spill registers.  The
+ * seed-sparse and one-thread-per-point methods are never candidates.  The
+ * winner is stored in the process-wide table used by
  * csize = 0 and returned in *best (may be NULL).  Synchronises `stream`.
  * Allocates no device memory. */
 CHESSFAD_API int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,
