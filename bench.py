@@ -339,12 +339,14 @@ def gpu_arm(args):
         micro32 = micro64 = None
         print(f"peak microbenchmark failed: {e}", file=sys.stderr)
     traffic = None
+    executed = None  # ncu's executed FP32 flops of the same kernel (FMA = 2), same gating as traffic
     tfile = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tfile):
         tj = json.load(open(tfile))
         ent = tj.get(f"{WORKLOAD}/fp32_comp/{f32['cfg']['method']}/c{c}")
         if ent and ent.get("source_hash") == kernel_source_hash():
             traffic = ent.get("dram_bytes_per_launch")
+            executed = ent.get("executed_flops_per_launch")
     c64 = f64["cfg"]["csize"]
     sym64 = f64["cfg"]["method"] == "symmetric"
     line = {
@@ -375,6 +377,9 @@ def gpu_arm(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
                      "frac": achieved / peak_fp32, "traffic": traffic,
                      "flops_per_launch": flops_launch,
+                     "executed_flops_per_launch": executed,
+                     "frac_executed": None if executed is None else executed / (avg_ms * 1e-3) / peak_fp32,
+                     "model_over_executed": None if executed is None else flops_launch / executed,
                      "kernel": ("sym_kernel<float,%d,ACKLEY,HVP>" if sym32 else "sweep_kernel<float,%d,ACKLEY,HVP>") % c,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
                      "peak_microbench": None if micro32 is None else micro32 / 1e12,
