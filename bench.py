@@ -631,7 +631,7 @@ def ragged_only(args):
 
 
 def report(args):
-    """Per-workload table for the benchmark spec: HVP/s (and Hessians/s) for every
+    """Per-workload table: HVP/s (and Hessians/s) for every
     named workload in both precisions, autotuned over both methods, plus the
     plain method at the workload's stated chunk size."""
     import torch

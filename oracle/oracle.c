@@ -29,7 +29,7 @@
  *      written once, generically, on hDuals.  O2 also carries the operation
  *      counters used to check the Sec. V analysis.
  *
- * Readings of the paper taken here (each is also listed in the design doc):
+ * Readings of the paper taken here:
  *  - csize need not divide n: nchunk = ceil(n/csize); the last chunk covers
  *    [cstart, n) and its seeds beyond n are zero (Sec. III-B assumes
  *    divisibility).
