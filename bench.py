@@ -525,7 +525,7 @@ def reference_arm(args):
 
     b = W.workload(WORKLOAD)
     c = 16
-    per = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    per = max(0.5, min(20.0, args.ref_budget / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_sample_time(b, c, per / 4)
     rates, secs, ms = [], 0.0, []
@@ -815,6 +815,8 @@ def main():
     ap.add_argument("--csize", type=int, default=32)
     ap.add_argument("--tpr", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
+    ap.add_argument("--ref-budget", type=float, default=150.0,
+                    help="reference arm: seconds of oracle work over all steps (bounded per step)")
     ap.add_argument("--e2e-slices", type=int, default=16,
                     help="slices of the end-to-end call (copies of one overlap the sweep of the next)")
     ap.add_argument("--method", choices=["plain", "symmetric", "symmetric_sparse"], default="plain")
