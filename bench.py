@@ -360,10 +360,11 @@ def gpu_arm(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 (compensated; f64 islands)",
+        "dtype": "f32",
         "data": "synthetic (seeded PCG64 draws of the workload's distributions)",
         "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": n, "batch": batch,
-                   "precision": "fp32_comp", **f32["cfg"], "l2": "flushed between timed steps (256 MiB write)",
+                   "precision": "fp32_comp (FP32 hDual arithmetic with compensated sums and dots, FP64 islands)",
+                   **f32["cfg"], "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": f"replicas x{world} (points independent, no collective)"},
         "fp64": {"value": v64, "unit": "HVP/s", "steps": f64["steps"], "ms_per_step": f64["total_ms"] / f64["steps"],
                  **{k: v for k, v in f64["cfg"].items()},
