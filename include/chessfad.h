@@ -131,7 +131,9 @@ typedef struct {
  *   threads_per_point symmetric method: threads sharing one point's
  *                     (row, chunk) items, 8..256 power of two (below 32 a
  *                     warp serves several points)
- * Zero in any field means "default" (method 0 is the plain method).  The
+ * Zero in any field means "default"; with csize 0, method 0 also means the
+ * default (tuned, else chessfad_default_config) method, otherwise method 0 is
+ * the plain method.  The
  * symmetric HVP stages a point's chunks on and above the diagonal chunks in
  * shared memory (about n (n + C) / 2 values per point) and sums whole rows,
  * reproducibly, for n up to about 280 (FP32) / 200 (FP64); beyond, it sums
@@ -199,8 +201,11 @@ CHESSFAD_API int chessfad_hvp_host(int fn, int n, long long batch, int csize, co
                                    const void *v_host, void *out_host, void *x_dev, void *v_dev, void *out_dev,
                                    const chessfad_fp_params *params, int prec, int slices, chessfad_stream_t stream);
 
-/* The configuration chessfad_hvp would use for csize = 0 (tuned entry if
- * present, else the default).  Host only; launches nothing. */
+/* The configuration chessfad_hvp would use for csize = 0: the tuned entry if
+ * present, else the default (n >= 4: the symmetric method at the Sec. V
+ * optimum csize = sqrt(n/2) rounded up to a power of two; n < 4: the plain
+ * method).  A call with csize != 0 and no configuration uses the plain method
+ * with that chunk size.  Host only; launches nothing. */
 CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg);
 
 /* Autotune the HVP launch configuration for (fn, n, prec) by timing the

@@ -59,6 +59,13 @@ static chessfad_config default_config(int fn, int n, long long batch, int prec)
     c.block_threads = 256;
     c.method = CHESSFAD_METHOD_PLAIN;
     c.threads_per_point = default_threads_per_point(n, batch);
+    if (n >= 4) {
+        // The symmetric method (about half the evaluations) at the Sec. V
+        // optimum c = sqrt(n/2), rounded up to a power of two.
+        c.method = CHESSFAD_METHOD_SYMMETRIC;
+        c.csize = std::min(cmax, next_pow2((int)std::ceil(std::sqrt(n / 2.0))));
+        c.block_threads = std::max(128, c.threads_per_point);
+    }
     return c;
 }
 
