@@ -92,6 +92,23 @@ def test_host_pipeline_argument_errors_without_gpu():
     assert lib.chessfad_hvp_host(0, 8, 0, 4, None, None, None, None, None, None, None, 0, 0, None) == 0
 
 
+def test_untuned_default_is_symmetric_at_the_sec5_chunk():
+    """Untuned default: the symmetric method for n >= 4 with csize near the
+    Sec. V optimum sqrt(n/2) (a power of two at or above it, capped by the
+    precision's register budget); the plain method below n = 4."""
+    import math
+
+    for fn in (0, 1, 2):
+        for prec in (0, 1):
+            for n in (4, 8, 16, 32, 64, 128, 256, 512):
+                c = cf.chessfad_default_config(fn, n, 4096, prec)
+                assert c.method == cf.SYMMETRIC, (fn, prec, n)
+                target = math.sqrt(n / 2)
+                assert c.csize >= min(target, 4) and (c.csize == 1 or c.csize / 2 < target), (n, c.csize)
+            for n in (1, 2, 3):
+                assert cf.chessfad_default_config(fn, n, 4096, prec).method == cf.PLAIN
+
+
 @pytest.mark.parametrize("fn", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_default_config_host_only(fn, prec):
