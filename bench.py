@@ -5,9 +5,20 @@ Workload: Ackley, n = 64, 65536 points, x ~ U[-5,5], v ~ U[-1,1], seed 1
 (PCG64), the configuration the headline metric is quoted on.  One step is one
 ``chessfad_hvp`` call over the whole batch: seeding, chunked-hDual propagation,
 row-times-v products and the in-kernel row reduction, all in the library's
-sweep kernel.  The headline ``value`` is compensated-FP32 HVP/s with inputs
-resident in HBM; the FP64 rate, a chunk-size sweep and the end-to-end rate
-through host buffers are reported beside it.
+sweep kernel.  The headline ``value`` is the FP64 rate (the paper's precision,
+Sec. IV) with inputs resident in HBM; the compensated-FP32 rate is reported
+beside it as a complete block (``fp32_comp``: rate, roofline, end-to-end rate,
+error), so "FP32-comp vs FP64" is one line.  ``workloads`` holds the other
+named workloads (Rosenbrock n=16 and n=256 with Hessians, Fletcher-Powell
+n=32) in both precisions, ``ragged_100k`` the 100000-request uneven batch.
+
+Roofline: the sweep kernels are bound by CUDA-core arithmetic (FP64 DFMA or
+FP32 FFMA pipe).  ``achieved`` = FP instructions the kernel executes per launch
+(ncu thread-instruction counts, FMA = 2 flops, recorded in
+``profiles/counts.json`` per point and keyed by a hash of the kernel sources;
+null when the sources changed since) / the launch's CUDA-event time;
+``peak`` = the library's FMA microbenchmark (``chessfad_peak_info``) measured in
+the same run on the same GPU.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the launching stream, with a 256 MiB buffer written between steps to flush
@@ -17,10 +28,14 @@ scaling; points are independent, there is no collective on the data path).
 
 ``--impl reference`` times the FP64 CPU oracle (the paper's sequential
 CHESS-VEC, Alg. 7, OpenMP over points) on the host cores instead.
+``--profile-kernels`` launches every kernel of ``profiles/counts.json`` once
+(the command ncu captures); ``--ingest-ncu CSV`` turns that capture into
+``profiles/counts.json``.
 """
 from __future__ import annotations
 
 import argparse
+import csv
 import hashlib
 import json
 import math
@@ -37,12 +52,13 @@ sys.path.insert(0, ROOT)
 METRIC = "Hessian-vector products/sec per function and n, FP32-comp vs FP64, 1 GB300"
 WORKLOAD = "ackley_n64"
 WORKLOAD_DESC = "Ackley n=64, 65536 points, x~U[-5,5], v~U[-1,1], seed 1 (PCG64)"
-SM_COUNT = 152
+# CUDA-core lanes per SM of sm_103 (GB300): 128 FP32 FMA lanes, and FP64 at
+# 1/64 of that (2 DFMA per clock per SM; GB300's nominal FP64 rate).  The SM
+# count and the clock come from the device at run time.
 FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-# FP64 DFMA lanes per SM: GB300's nominal 1.25 TFLOP/s FP64 at 2070 MHz over
-# 152 SMs is 3.97 flop/clk/SM, i.e. 2 DFMA per clock per SM.
 FP64_LANES_PER_SM = 2
+COUNTS_FILE = os.path.join(ROOT, "profiles", "counts.json")
+PREC_NAME = {0: "fp64", 1: "fp32_comp"}
 
 
 def sym_items(n: int, c: int) -> int:
@@ -85,22 +101,123 @@ def model_flops_hvp(fn: int, n: int, c: int, symmetric: bool = False) -> float:
     return sweeps * model_flops_eval(fn, n, c) + 2 * n * n
 
 
+def model_flops_hessian(fn: int, n: int, c: int, symmetric: bool = False) -> float:
+    """Model flops of one Hessian: the HVP's evaluations without the dots."""
+    nch = -(-n // c)
+    sweeps = sym_items(n, c) if symmetric else n * nch
+    return sweeps * model_flops_eval(fn, n, c)
+
+
 def model_flops_ackley(n: int, c: int, symmetric: bool = False) -> float:
     return model_flops_hvp(1, n, c, symmetric)
 
 
-# Sources that define the headline sweep kernel (the ncu traffic figure is
-# reported only while these are unchanged since the capture).
-KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "k_ackley_f32c.cu")
+def algorithmic_bytes(n: int, prec: int, kind: str) -> int:
+    """HBM bytes one point needs by definition: x, v, out (HVP) or x, H
+    (Hessian), s = 8 (FP64) or 4 (compensated FP32)."""
+    s = 8 if prec == 0 else 4
+    return 3 * n * s if kind == "hvp" else (n + n * n) * s
+
+
+# Sources that define the batched sweep kernels: the executed-instruction
+# counts and DRAM traffic in profiles/counts.json are used only while these
+# are unchanged since the capture.
+KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "point.cuh", "point.h", "k_*.cu")
 
 
 def kernel_source_hash() -> str:
+    import glob
+
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
-    for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(csrc, f), "rb").read())
+    for pat in KERNEL_SOURCES:
+        for p in sorted(glob.glob(os.path.join(csrc, pat))):
+            h.update(os.path.basename(p).encode())
+            h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
+
+def load_counts() -> dict:
+    """Executed FP instructions and DRAM bytes per point, per kernel key, from
+    the ncu capture of ``--profile-kernels``; entries whose sources changed
+    since the capture are dropped."""
+    if not os.path.exists(COUNTS_FILE):
+        return {}
+    tj = json.load(open(COUNTS_FILE))
+    h = kernel_source_hash()
+    return {k: v for k, v in tj.get("kernels", {}).items() if tj.get("source_hash") == h}
+
+
+def count_key(workload: str, prec: int, kind: str, method: str, c: int) -> str:
+    return f"{workload}/{PREC_NAME[prec]}/{kind}/{method}/c{c}"
+
+
+def device_peaks(cf, dev_index: int) -> dict:
+    """FMA peaks of this GPU: the library's microbenchmark (measured now, with
+    the SM clock it saw) and the unit-count figure SMs x lanes x 2 x max SM
+    clock (SM count from the device, max clock from nvidia-smi)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    max_mhz = None
+    try:
+        q = subprocess.run(["nvidia-smi", f"--id={dev_index}", "--query-gpu=clocks.max.sm",
+                            "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=20)
+        max_mhz = float(q.stdout.strip().splitlines()[0])
+    except Exception:
+        max_mhz = None
+    out = {"sms": sms, "sm_max_mhz": max_mhz}
+    for prec, lanes in ((0, FP64_LANES_PER_SM), (1, FP32_LANES_PER_SM)):
+        try:
+            f, mhz = cf.chessfad_peak_info(prec)
+        except Exception as e:  # report, do not hide
+            print(f"peak microbenchmark failed: {e}", file=sys.stderr)
+            f, mhz = None, None
+        out[PREC_NAME[prec]] = {
+            "microbench": f, "microbench_sm_mhz": mhz,
+            "derived": None if max_mhz is None else sms * lanes * 2 * max_mhz * 1e6,
+            "derived_note": f"{sms} SMs x {lanes} {'DFMA' if prec == 0 else 'FFMA'} lanes x 2 flop x "
+                            f"{max_mhz} MHz (max SM clock)"}
+    return out
+
+
+def roofline_entry(counts: dict, key: str, units: int, ms: float, prec: int, peaks: dict, n: int, kind: str,
+                   model_flops_per_unit: float, kernel: str) -> dict:
+    """The ALU roofline of one kernel launch of `units` points taking `ms`."""
+    p = peaks[PREC_NAME[prec]]
+    ent = counts.get(key)
+    executed = None if ent is None else ent["executed_flops_per_unit"] * units
+    traffic = None if ent is None or ent.get("dram_bytes_per_unit") is None else ent["dram_bytes_per_unit"] * units
+    achieved = None if executed is None else executed / (ms * 1e-3)
+    model = model_flops_per_unit * units
+    algo = algorithmic_bytes(n, prec, kind) * units
+    return {
+        "bound": "alu", "unit": "TFLOP/s", "kernel": kernel,
+        "achieved": None if achieved is None else achieved / 1e12,
+        "peak": None if p["microbench"] is None else p["microbench"] / 1e12,
+        "frac": None if achieved is None or p["microbench"] is None else achieved / p["microbench"],
+        "peak_source": f"measured: chessfad_peak_info({PREC_NAME[prec]}) FMA microbenchmark in this run, "
+                       f"SM clock {p['microbench_sm_mhz'] and round(p['microbench_sm_mhz'])} MHz",
+        "peak_derived": None if p["derived"] is None else p["derived"] / 1e12,
+        "frac_of_derived": None if achieved is None or p["derived"] is None else achieved / p["derived"],
+        "executed_flops_per_launch": executed,
+        "model_flops_per_launch": model,
+        "model_over_executed": None if executed is None else model / executed,
+        "traffic": traffic,
+        "algorithmic_bytes_per_launch": algo,
+        "dram_gbs_algorithmic": algo / (ms * 1e-3) / 1e9,
+        "dram_gbs_measured_traffic": None if traffic is None else traffic / (ms * 1e-3) / 1e9,
+        "counts_key": key, "counts_present": ent is not None,
+    }
+
+
+def kernel_name(method: str, prec: int, c: int, fn: int, kind: str) -> str:
+    t = "double" if prec == 0 else "float"
+    f = {0: "ROSENBROCK", 1: "ACKLEY", 2: "FP"}[fn]
+    k = "HVP" if kind == "hvp" else "HESSIAN"
+    base = "sym_kernel" if method in ("symmetric", "symmetric_sparse") else (
+        "point_kernel" if method == "point" else "sweep_kernel")
+    return f"{base}<{t},{c},{f},{k}>"
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
@@ -205,8 +322,192 @@ def timed_steps(fn_step, steps, warmup, stream, flush_buf):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def _checked(st, what):
+    import paper_2410_22575_gb300 as cf
+
+    if st != 0:
+        raise cf.ChessfadError(st, what)
+
+
+def headline_arm(cf, b, prec, args, world, dev, stream, flush, peaks, counts):
+    """The named workload in one precision: autotuned HVP config, K timed
+    steps (clocks sampled), then the same through host buffers (e2e)."""
+    import torch
+
+    dt = torch.float64 if prec == cf.FP64 else torch.float32
+    fn, n, batch = b.fn, b.n, b.batch
+    x = torch.tensor(b.x, dtype=dt, device=dev)
+    v = torch.tensor(b.v, dtype=dt, device=dev)
+    out = torch.empty_like(x)
+    cfg = cf.chessfad_autotune_hvp(fn, n, batch, x, v, out, None, prec, stream)
+
+    def step():
+        _checked(cf.chessfad_hvp(fn, n, batch, 0, x, v, out, None, prec, stream), "chessfad_hvp")
+
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        ms = timed_steps(step, args.steps, args.warmup, stream, flush)
+    clocks = clk.summary()
+    torch.cuda.synchronize()
+    barrier(world)
+    tot = max_over_ranks(world, sum(ms), dev)
+    per = tot / len(ms)
+    cd = cfg.as_dict()
+    sym = cd["method"] == "symmetric"
+    key = count_key(WORKLOAD, prec, "hvp", cd["method"], cfg.csize)
+    roof = roofline_entry(counts, key, batch, sum(ms) / len(ms), prec, peaks, n, "hvp",
+                          model_flops_hvp(fn, n, cfg.csize, sym), kernel_name(cd["method"], prec, cfg.csize, fn, "hvp"))
+    res = {"value": world * batch / (per * 1e-3), "unit": "HVP/s", "steps": len(ms), "ms_per_step": per,
+           "config": cd, "roofline": roof, "clocks": clocks, "_out": out.double().cpu().numpy(),
+           "_x": x.double().cpu().numpy(), "_v": v.double().cpu().numpy()}
+
+    # chunk-size sweep (shorter), same precision, both methods
+    sweep = {}
+    for c in (4, 8, 16, 32):
+        info = cf.chessfad_kernel_info(fn, prec, c, True)
+        if info["local_bytes"] > 48:
+            sweep[str(c)] = {"skipped": "spills registers", **info}
+            continue
+        ent = dict(info)
+        for mname, ccfg in (("plain", cf.Config(c, 1, 256)), ("symmetric", cf.Config(c, 0, 0, cf.SYMMETRIC, 64))):
+            def stc(ccfg=ccfg):
+                _checked(cf.chessfad_hvp_config(fn, n, batch, ccfg, x, v, out, None, prec, stream), "chessfad_hvp")
+
+            k = max(1, min(3, args.steps))
+            m = timed_steps(stc, k, 1, stream, flush)
+            t = max_over_ranks(world, sum(m), dev) / k
+            ent[mname] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t}
+        sweep[str(c)] = ent
+    res["chunk_sweep"] = sweep
+
+    # seed-sparse symmetric method (a different arithmetic: reported beside
+    # the headline, never as it)
+    sparse = {}
+    for c in (4, 8):
+        scfg = cf.Config(c, 0, 128, cf.SYMMETRIC_SPARSE, 64)
+
+        def sts(scfg=scfg):
+            _checked(cf.chessfad_hvp_config(fn, n, batch, scfg, x, v, out, None, prec, stream), "chessfad_hvp")
+
+        k = max(1, min(3, args.steps))
+        m = timed_steps(sts, k, 1, stream, flush)
+        t = max_over_ranks(world, sum(m), dev) / k
+        sparse[str(c)] = {**scfg.as_dict(), "hvp_per_s": world * batch / (t * 1e-3), "ms": t}
+    res["seed_sparse"] = sparse
+    del x, v, out
+
+    # end to end through the public host-buffer call: pinned host x, v ->
+    # device -> sweeps -> host out, copies of consecutive slices overlapping
+    # the sweeps, all inside the events
+    xh = torch.tensor(b.x, dtype=dt).pin_memory()
+    vh = torch.tensor(b.v, dtype=dt).pin_memory()
+    oh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(xh, device=dev)
+    vd = torch.empty_like(vh, device=dev)
+    od = torch.empty_like(xh, device=dev)
+
+    def e2e_step():
+        _checked(cf.chessfad_hvp_host(fn, n, batch, 0, xh, vh, oh, xd, vd, od, None, prec, args.e2e_slices, stream),
+                 "chessfad_hvp_host")
+
+    barrier(world)
+    ms_e2e = timed_steps(e2e_step, args.steps, args.warmup, stream, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    tot_e2e = max_over_ranks(world, sum(ms_e2e), dev)
+    s = 8 if prec == cf.FP64 else 4
+    res["e2e"] = {"value": world * batch * len(ms_e2e) / (tot_e2e * 1e-3), "unit": "HVP/s",
+                  "h2d_bytes_per_step": 2 * batch * n * s, "d2h_bytes_per_step": batch * n * s,
+                  "api": "chessfad_hvp_host (pinned host buffers)", "slices": args.e2e_slices,
+                  "ms_per_step": tot_e2e / len(ms_e2e)}
+    return res
+
+
+# The other named workloads and what is measured on each.  C1 (Rosenbrock
+# n=16) is quoted in FP64 with c=4 by the plain method, HVP and Hessian; C3
+# (Fletcher-Powell n=32) in FP64 and in compensated FP32 (FP64 residuals);
+# C4 (Rosenbrock n=256) HVP and Hessian, autotuned, in both precisions.
+WORKLOAD_ROWS = (
+    ("rosenbrock_n16", "hvp", "stated", 0),
+    ("rosenbrock_n16", "hessian", "stated", 0),
+    ("rosenbrock_n16", "hvp", "tuned", 0),
+    ("rosenbrock_n16", "hessian", "tuned", 0),
+    ("rosenbrock_n16", "hvp", "tuned", 1),
+    ("rosenbrock_n16", "hessian", "tuned", 1),
+    ("fletcher_powell_n32", "hvp", "tuned", 0),
+    ("fletcher_powell_n32", "hvp", "tuned", 1),
+    ("rosenbrock_n256", "hvp", "tuned", 0),
+    ("rosenbrock_n256", "hessian", "tuned", 0),
+    ("rosenbrock_n256", "hvp", "tuned", 1),
+    ("rosenbrock_n256", "hessian", "tuned", 1),
+)
+
+
+def workloads_arm(cf, args, world, dev, stream, flush, peaks, counts):
+    """Every row of WORKLOAD_ROWS: rate, roofline (executed flops when the
+    counts are current), DRAM GB/s; the outputs are kept for the oracle leg."""
+    import torch
+    from paper_2410_22575_gb300 import workloads as W
+
+    rows = {}
+    for name, kind, how, prec in WORKLOAD_ROWS:
+        b = W.workload(name)
+        dt = torch.float64 if prec == cf.FP64 else torch.float32
+        keep, params = [], None
+        if b.fn == W.FLETCHER_POWELL:
+            keep = [torch.tensor(a, dtype=torch.float64, device=dev) for a in (b.fp.A, b.fp.B, b.fp.E)]
+            params = cf.fp_params(*keep)
+        x = torch.tensor(b.x, dtype=dt, device=dev)
+        v = torch.tensor(b.v, dtype=dt, device=dev)
+        if kind == "hvp":
+            out = torch.empty_like(x)
+            if how == "stated":
+                cfg = cf.Config(4, 1, 256, cf.PLAIN, 0)
+            else:
+                cfg = cf.chessfad_autotune_hvp(b.fn, b.n, b.batch, x, v, out, params, prec, stream)
+
+            def step(cfg=cfg):
+                _checked(cf.chessfad_hvp_config(b.fn, b.n, b.batch, cfg, x, v, out, params, prec, stream),
+                         "chessfad_hvp_config")
+        else:
+            out = torch.empty((b.batch, b.n, b.n), dtype=dt, device=dev)
+            if how == "stated":
+                cfg = cf.Config(4, 1, 256, cf.PLAIN, 0)
+            else:
+                cfg = cf.chessfad_autotune_hessian(b.fn, b.n, b.batch, x, out, params, prec, stream)
+
+            def step(cfg=cfg):
+                _checked(cf.chessfad_hessian_config(b.fn, b.n, b.batch, cfg, x, out, params, prec, stream),
+                         "chessfad_hessian_config")
+        cfg = cf.chessfad_resolve_config(b.fn, b.n, b.batch, prec, cfg, hvp=(kind == "hvp"))
+        cd = cfg.as_dict()
+        k = max(1, min(args.steps, args.workload_steps))
+        barrier(world)
+        ms = timed_steps(step, k, 2, stream, flush)
+        tot = max_over_ranks(world, sum(ms), dev)
+        per = tot / len(ms)
+        sym = cd["method"] == "symmetric"
+        mf = (model_flops_hvp if kind == "hvp" else model_flops_hessian)(b.fn, b.n, cfg.csize, sym)
+        key = count_key(name, prec, kind, cd["method"], cfg.csize)
+        roof = roofline_entry(counts, key, b.batch, sum(ms) / len(ms), prec, peaks, b.n, kind, mf,
+                              kernel_name(cd["method"], prec, cfg.csize, b.fn, kind))
+        rate = world * b.batch / (per * 1e-3)
+        row = {"workload": name, "function": W.FN_NAMES[b.fn], "n": b.n, "batch": b.batch,
+               "precision": PREC_NAME[prec], "kind": kind, "configuration": how, "config": cd,
+               ("hvp_per_s" if kind == "hvp" else "hessians_per_s"): rate, "ms": per, "steps": len(ms),
+               "roofline": roof}
+        row["_out"] = out.double().cpu().numpy() if kind == "hvp" else out.cpu().numpy()
+        row["_x"] = x.double().cpu().numpy()
+        row["_v"] = v.double().cpu().numpy()
+        row["_b"] = b
+        rows[f"{name}/{PREC_NAME[prec]}/{kind}/{how}"] = row
+        print(json.dumps({k2: v2 for k2, v2 in row.items() if not k2.startswith("_")}), file=sys.stderr, flush=True)
+        del x, v, out, keep
+    return rows
+
+
 def gpu_arm(args):
-    import numpy as np
     import torch
 
     import paper_2410_22575_gb300 as cf
@@ -220,98 +521,12 @@ def gpu_arm(args):
     fn, n, batch = b.fn, b.n, b.batch
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = device_peaks(cf, local)
+    counts = load_counts()
 
-    res = {}
-    for prec, dt in ((cf.FP32_COMP, torch.float32), (cf.FP64, torch.float64)):
-        x = torch.tensor(b.x, dtype=dt, device=dev)
-        v = torch.tensor(b.v, dtype=dt, device=dev)
-        out = torch.empty_like(x)
-        cfg = cf.chessfad_autotune_hvp(fn, n, batch, x, v, out, None, prec, stream)
-        steps = args.steps if prec == cf.FP32_COMP else max(1, min(args.steps, args.fp64_steps))
-
-        def step():
-            st = cf.chessfad_hvp(fn, n, batch, 0, x, v, out, None, prec, stream)
-            if st != 0:
-                raise cf.ChessfadError(st, "chessfad_hvp")
-
-        barrier(world)
-        torch.cuda.synchronize()
-        if prec == cf.FP32_COMP:
-            with ClockSampler(local) as clk:
-                ms = timed_steps(step, steps, args.warmup, stream, flush)
-            clocks = clk.summary()
-        else:
-            ms = timed_steps(step, steps, args.warmup, stream, flush)
-        torch.cuda.synchronize()
-        barrier(world)
-        tot = max_over_ranks(world, sum(ms), dev)
-        res[prec] = {"cfg": cfg.as_dict(), "ms": ms, "total_ms": tot, "steps": steps,
-                     "out_sample": out[:256].double().cpu().numpy(), "x32": x[:256].double().cpu().numpy(),
-                     "v32": v[:256].double().cpu().numpy()}
-        if prec == cf.FP32_COMP:
-            res[prec]["clocks"] = clocks
-
-        # chunk-size sweep (shorter), same precision
-        sweep = {}
-        for c in (4, 8, 16, 32):
-            info = cf.chessfad_kernel_info(fn, prec, c, True)
-            if info["local_bytes"] > 48:
-                sweep[str(c)] = {"skipped": "spills registers", **info}
-                continue
-            ent = dict(info)
-            for mname, ccfg in (("plain", cf.Config(c, 1, 256)), ("symmetric", cf.Config(c, 0, 0, cf.SYMMETRIC, 64))):
-                def stc(ccfg=ccfg):
-                    st = cf.chessfad_hvp_config(fn, n, batch, ccfg, x, v, out, None, prec, stream)
-                    if st != 0:
-                        raise cf.ChessfadError(st, "chessfad_hvp")
-
-                k = max(1, min(5, steps))
-                m = timed_steps(stc, k, 1, stream, flush)
-                t = max_over_ranks(world, sum(m), dev) / k
-                ent[mname] = {"hvp_per_s": world * batch / (t * 1e-3), "ms": t}
-            sweep[str(c)] = ent
-        res[prec]["sweep"] = sweep
-
-        # seed-sparse symmetric method (a different arithmetic: reported beside
-        # the headline, never as it)
-        sparse = {}
-        for c in (4, 8):
-            scfg = cf.Config(c, 0, 128, cf.SYMMETRIC_SPARSE, 64)
-
-            def sts(scfg=scfg):
-                st = cf.chessfad_hvp_config(fn, n, batch, scfg, x, v, out, None, prec, stream)
-                if st != 0:
-                    raise cf.ChessfadError(st, "chessfad_hvp")
-
-            k = max(1, min(5, steps))
-            m = timed_steps(sts, k, 1, stream, flush)
-            t = max_over_ranks(world, sum(m), dev) / k
-            sparse[str(c)] = {**scfg.as_dict(), "hvp_per_s": world * batch / (t * 1e-3), "ms": t}
-        res[prec]["sparse"] = sparse
-        del x, v, out
-
-    # ---- end to end: pinned host buffers -> device -> hvp -> host, FP32-comp
-    xh = torch.tensor(b.x, dtype=torch.float32).pin_memory()
-    vh = torch.tensor(b.v, dtype=torch.float32).pin_memory()
-    oh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(xh, device=dev)
-    vd = torch.empty_like(vh, device=dev)
-    od = torch.empty_like(xh, device=dev)
-
-    def e2e_step():
-        # one C-ABI call: pinned host x, v -> device -> sweeps -> host out,
-        # copies of consecutive slices overlapping the sweeps
-        st = cf.chessfad_hvp_host(fn, n, batch, 0, xh, vh, oh, xd, vd, od, None, cf.FP32_COMP, args.e2e_slices,
-                                  stream)
-        if st != 0:
-            raise cf.ChessfadError(st, "chessfad_hvp_host")
-
-    barrier(world)
-    ms_e2e = timed_steps(e2e_step, args.steps, args.warmup, stream, flush)
-    torch.cuda.synchronize()
-    barrier(world)
-    tot_e2e = max_over_ranks(world, sum(ms_e2e), dev)
-
+    f64 = headline_arm(cf, b, cf.FP64, args, world, dev, stream, flush, peaks, counts)
+    f32 = headline_arm(cf, b, cf.FP32_COMP, args, world, dev, stream, flush, peaks, counts)
+    rows = {} if args.no_workloads else workloads_arm(cf, args, world, dev, stream, flush, peaks, counts)
     ragged = None if args.no_ragged else ragged_arm(args, world, dev, stream, flush)
 
     if rank != 0:
@@ -321,84 +536,64 @@ def gpu_arm(args):
             dist.destroy_process_group()
         return
 
-    f32 = res[cf.FP32_COMP]
-    f64 = res[cf.FP64]
-    value = world * batch * f32["steps"] / (f32["total_ms"] * 1e-3)
-    v64 = world * batch * f64["steps"] / (f64["total_ms"] * 1e-3)
-    c = f32["cfg"]["csize"]
-    sym32 = f32["cfg"]["method"] == "symmetric"
-    flops_launch = model_flops_ackley(n, c, sym32) * batch
-    avg_ms = sum(f32["ms"]) / len(f32["ms"])
-    peak_fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
-    peak_fp64 = SM_COUNT * FP64_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6
-    achieved = flops_launch / (avg_ms * 1e-3)
-    try:
-        micro32 = cf.chessfad_peak_flops(cf.FP32_COMP)
-        micro64 = cf.chessfad_peak_flops(cf.FP64)
-    except Exception as e:  # report, do not hide
-        micro32 = micro64 = None
-        print(f"peak microbenchmark failed: {e}", file=sys.stderr)
-    traffic = None
-    executed = None  # ncu's executed FP32 flops of the same kernel (FMA = 2), same gating as traffic
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        tj = json.load(open(tfile))
-        ent = tj.get(f"{WORKLOAD}/fp32_comp/{f32['cfg']['method']}/c{c}")
-        if ent and ent.get("source_hash") == kernel_source_hash():
-            traffic = ent.get("dram_bytes_per_launch")
-            executed = ent.get("executed_flops_per_launch")
-    c64 = f64["cfg"]["csize"]
-    sym64 = f64["cfg"]["method"] == "symmetric"
+    config = headline_config(batch, world)
+    pub = lambda d: {k: v for k, v in d.items() if not k.startswith("_")}
     line = {
         "metric": METRIC,
-        "value": value,
+        "value": f64["value"],
         "unit": "HVP/s",
         "n_gpus": world,
-        "steps": f32["steps"],
+        "steps": f64["steps"],
         "warmup": args.warmup,
-        "ms_per_step": f32["total_ms"] / f32["steps"],
+        "ms_per_step": f64["ms_per_step"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f64",
         "data": "synthetic (seeded PCG64 draws of the workload's distributions)",
-        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": n, "batch": batch,
-                   "precision": "fp32_comp (FP32 hDual arithmetic with compensated sums and dots, FP64 islands)",
-                   **f32["cfg"], "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world} (points independent, no collective)"},
-        "fp64": {"value": v64, "unit": "HVP/s", "steps": f64["steps"], "ms_per_step": f64["total_ms"] / f64["steps"],
-                 **{k: v for k, v in f64["cfg"].items()},
-                 "model_tflops": model_flops_ackley(n, c64, sym64) * batch / (f64["total_ms"] / f64["steps"] * 1e-3) / 1e12,
-                 "peak_tflops_derived": peak_fp64 / 1e12},
-        "fp32_over_fp64": value / v64,
-        "chunk_sweep": {"fp32_comp": f32["sweep"], "fp64": f64["sweep"]},
-        "seed_sparse": {"fp32_comp": f32["sparse"], "fp64": f64["sparse"],
+        "config": config,
+        "launch": f64["config"],
+        "roofline": f64["roofline"],
+        "e2e": f64["e2e"],
+        "gpu_launches": f64["steps"],
+        "clocks": f64["clocks"],
+        "fp32_comp": {"value": f32["value"], "unit": "HVP/s", "dtype": "f32",
+                      "precision": "FP32 hDual arithmetic with compensated sums and dots, FP64 islands",
+                      "steps": f32["steps"], "ms_per_step": f32["ms_per_step"], "launch": f32["config"],
+                      "roofline": f32["roofline"], "e2e": f32["e2e"], "clocks": f32["clocks"]},
+        "fp32_over_fp64": f32["value"] / f64["value"],
+        "chunk_sweep": {"fp64": f64["chunk_sweep"], "fp32_comp": f32["chunk_sweep"]},
+        "seed_sparse": {"fp64": f64["seed_sparse"], "fp32_comp": f32["seed_sparse"],
                         "method": "symmetric, seed-sparse propagation (skips variables whose seed has no "
                                   "derivative part); equal to the dense result for finite inputs"},
-        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_fp32 / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved / peak_fp32, "traffic": traffic,
-                     "flops_per_launch": flops_launch,
-                     "executed_flops_per_launch": executed,
-                     "frac_executed": None if executed is None else executed / (avg_ms * 1e-3) / peak_fp32,
-                     "model_over_executed": None if executed is None else flops_launch / executed,
-                     "kernel": ("sym_kernel<float,%d,ACKLEY,HVP>" if sym32 else "sweep_kernel<float,%d,ACKLEY,HVP>") % c,
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                     "peak_microbench": None if micro32 is None else micro32 / 1e12,
-                     "frac_of_microbench": None if micro32 is None else achieved / micro32,
-                     "fp64_peak_microbench": None if micro64 is None else micro64 / 1e12},
-        "e2e": {"value": world * batch * args.steps / (tot_e2e * 1e-3), "unit": "HVP/s",
-                "h2d_bytes_per_step": 2 * batch * n * 4, "d2h_bytes_per_step": batch * n * 4,
-                "api": "chessfad_hvp_host (pinned host buffers)", "slices": args.e2e_slices},
-        "gpu_launches": f32["steps"],
-        "clocks": f32.get("clocks"),
+        "peaks": {k: v for k, v in peaks.items()},
+        "counts_source_hash": kernel_source_hash(),
+        "counts_current": bool(counts),
     }
+    if rows:
+        line["workloads"] = {k: pub(r) for k, r in rows.items()}
     if ragged is not None:
-        line["ragged_100k"] = {k: v for k, v in ragged.items() if not k.startswith("_")}
+        line["ragged_100k"] = pub(ragged)
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(b, c, f32, f64, args)
+        # The oracle leg: CPU baselines and every error against the oracle.
+        line["cpu_baseline"] = cpu_baseline(b, 8, args)
+        line["error_vs_oracle"] = headline_error(f64, 0)
+        line["fp32_comp"]["error_vs_oracle"] = headline_error(f32, 1)
+        for k, r in rows.items():
+            line["workloads"][k]["error_vs_oracle"] = workload_error(r)
         if ragged is not None:
-            line["ragged_100k"]["error_vs_oracle_sample"] = ragged_error(ragged)
+            e, t_all = ragged_error_all(ragged)
+            line["ragged_100k"]["error_vs_oracle"] = e
+            line["ragged_100k"]["cpu_baseline"] = ragged_cpu_baseline(ragged, t_all, args)
     print(json.dumps(line))
+
+
+def headline_config(batch: int, world: int) -> dict:
+    """The workload description both arms print (the GPU launch configuration
+    is reported separately under "launch")."""
+    return {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": 64, "batch": batch,
+            "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas x{world} (points independent, no collective)"}
 
 
 # ------------------------------------------------------------------ uneven batch
@@ -415,7 +610,6 @@ def ragged_arm(args, world, dev, stream, flush):
     """The 100000-request uneven batch (three functions, n log-uniform in
     [2, 512], seed 4) in compensated FP32: one persistent launch per step,
     replayed from a captured CUDA graph."""
-    import numpy as np
     import torch
 
     import paper_2410_22575_gb300 as cf
@@ -452,30 +646,113 @@ def ragged_arm(args, world, dev, stream, flush):
             "method": "plain; symmetric (SC-HESS-VEC) for Fletcher-Powell n >= 128",
             "workspace_bytes": plan.info["workspace_bytes"], "plan_seconds": t_plan,
             "model_tflops": flops / (per * 1e-3) / 1e12,
-            "_out": out, "_x": x, "_v": v, "_rg": rg}
+            "_out": out.double().cpu().numpy(), "_x": x.double().cpu().numpy(), "_v": v.double().cpu().numpy(),
+            "_rg": rg, "_c": c}
 
 
-def ragged_error(r):
-    """Oracle check of 200 requests of the uneven batch (cpu_baseline leg)."""
-    import numpy as np
+# ------------------------------------------------------------------ oracle leg
+# Everything below runs the oracle (test infrastructure): the CPU baselines and
+# the errors of the GPU outputs against it.  It runs on rank 0 at N = 1 only.
+def headline_error(res, prec):
+    """Per-point normalised error of the headline outputs over the whole
+    batch (the oracle is given the values the device held)."""
+    import oracle
+    from paper_2410_22575_gb300 import metrics
 
+    ref, hn = oracle.hvp(1, res["_x"], res["_v"], with_norm=True)
+    e = metrics.hvp_errors(res["_out"], ref, hn, res["_v"])
+    bound = metrics.FP64_BOUND if prec == 0 else metrics.FP32_COMP_BOUND
+    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound)}
+
+
+def workload_error(row):
+    import oracle
+    from paper_2410_22575_gb300 import metrics, workloads as W
+
+    b = row["_b"]
+    p = None if b.fp is None else oracle.FPParams(b.fp.A, b.fp.B, b.fp.E)
+    if row["kind"] == "hvp":
+        ref, hn = oracle.hvp(b.fn, row["_x"], row["_v"], p, with_norm=True)
+        e = metrics.hvp_errors(row["_out"], ref, hn, row["_v"])
+    else:
+        e = metrics.hessian_errors(row["_out"], oracle.hessian_batch(b.fn, row["_x"], p))
+    bound = metrics.FP64_BOUND if row["precision"] == "fp64" else metrics.FP32_COMP_BOUND
+    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound)}
+
+
+def ragged_error_all(r):
+    """Error of every one of the 100000 requests against the oracle (closed
+    forms, O1); also returns the oracle's wall time on all of them."""
     import oracle
     from paper_2410_22575_gb300 import metrics
 
     rg = r["_rg"]
-    idx = np.sort(np.random.Generator(np.random.PCG64(0)).choice(rg.nreq, 200, replace=False))
-    sub = rg.subset(idx)
-    xh = r["_x"].double().cpu().numpy()
-    vh = r["_v"].double().cpu().numpy()
-    oh = r["_out"].double().cpu().numpy()
-    take = lambda a: np.concatenate([a[rg.offs[q]:rg.offs[q] + rg.ns[q]] for q in idx])
-    xs, vs, got = take(xh), take(vh), take(oh)
-    ref, hn = oracle.hvp_ragged(sub.fns, sub.ns, sub.offs, sub.eoffs, xs, vs, rg.fp.A, rg.fp.B, rg.Epack, rg.ld)
-    e = metrics.ragged_hvp_errors(got, ref, hn, vs, sub.ns, sub.offs)
-    return {**metrics.summary(e), "requests": len(idx)}
+    t0 = time.perf_counter()
+    ref, hn = oracle.hvp_ragged(rg.fns, rg.ns, rg.offs, rg.eoffs, r["_x"], r["_v"], rg.fp.A, rg.fp.B, rg.Epack,
+                                rg.ld)
+    t_all = time.perf_counter() - t0
+    e = metrics.ragged_hvp_errors(r["_out"], ref, hn, r["_v"], rg.ns, rg.offs)
+    per_fn = {}
+    for f, name in ((0, "rosenbrock"), (1, "ackley"), (2, "fletcher_powell")):
+        sel = rg.fns == f
+        per_fn[name] = metrics.summary(e[sel])
+    return {**metrics.summary(e), "requests": int(len(e)), "bound": metrics.FP32_COMP_BOUND,
+            "within_bound": bool(e.max() <= metrics.FP32_COMP_BOUND), "per_function": per_fn}, t_all
 
 
-# ------------------------------------------------------------------ CPU oracle
+def ragged_cpu_baseline(r, t_closed_form_all, args):
+    """The oracle's CHESS-VEC (Alg. 7, FP64, the plan's chunk size) on a random
+    sample of the 100000 requests whose model cost is bounded, run on all host
+    cores (one request per thread), extrapolated to all requests by the model
+    flops of each request; and the closed-form oracle on all of them."""
+    import concurrent.futures as futures
+
+    import numpy as np
+
+    import oracle
+
+    rg = r["_rg"]
+    c = r["_c"]
+    oracle.build()
+    cost = np.array([model_flops_hvp(int(f), int(n), c) for f, n in zip(rg.fns, rg.ns)])
+    rng = np.random.Generator(np.random.PCG64(5))
+    cap = args.ragged_cpu_cap
+    cand = np.nonzero(cost <= cap)[0]
+    order = rng.permutation(cand)
+    p = oracle.FPParams(rg.fp.A, rg.fp.B, rg.fp.E)
+    cores = oracle.num_threads()
+    budget = args.cpu_seconds
+
+    def one(q):
+        o, n = int(rg.offs[q]), int(rg.ns[q])
+        pe = oracle.FPParams(rg.fp.A[:n, :n], rg.fp.B[:n, :n], rg.Epack[rg.eoffs[q]:rg.eoffs[q] + n]) \
+            if rg.fns[q] == 2 else None
+        oracle.chess_vec(int(rg.fns[q]), r["_x"][o:o + n], r["_v"][o:o + n], c, pe)
+
+    # grow the sample in rounds until the budget is spent
+    done = 0
+    t_run = 0.0
+    with futures.ThreadPoolExecutor(cores) as ex:
+        while done < len(order) and t_run < budget:
+            take = order[done:done + max(cores * 8, 64)]
+            t0 = time.perf_counter()
+            list(ex.map(one, take))
+            t_run += time.perf_counter() - t0
+            done += len(take)
+    sample = order[:done]
+    frac_flops = cost.sum() / cost[sample].sum()
+    t_all_est = t_run * frac_flops
+    return {"value": rg.nreq / t_all_est, "unit": "HVP/s", "cores": cores, "kind": "oracle",
+            "extrapolated": True,
+            "sample": (f"CHESS-VEC (Alg. 7) FP64 c={c} on {len(sample)} random requests with model cost <= "
+                       f"{cap:.0e} flops ({cost[sample].sum() / cost.sum() * 100:.3f} % of the batch's model "
+                       f"flops), {t_run:.1f} s on {cores} threads; scaled to all {rg.nreq} requests by model "
+                       f"flops"),
+            "sample_requests": int(len(sample)), "sample_seconds": t_run,
+            "closed_form_all_requests_seconds": t_closed_form_all,
+            "closed_form_hvp_per_s": rg.nreq / t_closed_form_all}
+
+
 def cpu_sample_time(b, c, target_s):
     """Time the oracle's CHESS-VEC (Alg. 7, FP64, OpenMP over points) on a
     prefix of the batch sized for about target_s seconds; return
@@ -494,29 +771,24 @@ def cpu_sample_time(b, c, target_s):
     return m / dt, m, dt, out
 
 
-def cpu_baseline(b, c, f32, f64, args):
-    import numpy as np
-
+def cpu_baseline(b, c, args):
+    """The oracle's CHESS-VEC (FP64, chunk c) on a timed prefix of the
+    headline batch, and the closed-form oracle on the same prefix."""
     import oracle
-    from paper_2410_22575_gb300 import metrics
 
     rate, m, dt, _ = cpu_sample_time(b, c, args.cpu_seconds)
-    # closed-form oracle (O1) on the same prefix, and the GPU's error against it
     t0 = time.perf_counter()
     oracle.hvp(b.fn, b.x[:m], b.v[:m])
     t_cf = time.perf_counter() - t0
-    acc = {}
-    for name, r in (("fp32_comp", f32), ("fp64", f64)):
-        ref, hn = oracle.hvp(b.fn, r["x32"], r["v32"], with_norm=True)
-        e = metrics.hvp_errors(r["out_sample"], ref, hn, r["v32"])
-        acc[name] = metrics.summary(e)
     return {"value": rate, "unit": "HVP/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {m} of {b.batch} points, CHESS-VEC (Alg. 7) FP64 with c={c}, {dt:.1f} s",
-            "closed_form_hvp_per_s": m / t_cf,
-            "gpu_error_vs_oracle_first256": acc}
+            "closed_form_hvp_per_s": m / t_cf}
 
 
 def reference_arm(args):
+    """The oracle's CHESS-VEC (Alg. 7, FP64, c = 8) on the host cores: each
+    step a prefix of the headline batch sized to the step budget; ms_per_step
+    is the measured time of that step."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -525,30 +797,197 @@ def reference_arm(args):
     from paper_2410_22575_gb300 import workloads as W
 
     b = W.workload(WORKLOAD)
-    c = 16
+    c = 8
     per = max(0.5, min(20.0, args.ref_budget / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_sample_time(b, c, per / 4)
-    rates, secs, ms = [], 0.0, []
-    sample = 0
+    rates, secs, pts = [], [], []
     for _ in range(args.steps):
         r, m, dt, _ = cpu_sample_time(b, c, per)
         rates.append(r)
-        secs += dt
-        sample = m
-        ms.append(dt * 1e3 * b.batch / m)
-    value = statistics.median(rates)
+        secs.append(dt)
+        pts.append(m)
+    value = sum(pts) / sum(secs)
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "HVP/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(ms),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded PCG64 draws of the workload's distributions)",
-        "config": {"workload": f"{WORKLOAD}: {WORKLOAD_DESC}", "function": "ackley", "n": 64, "batch": b.batch,
-                   "precision": "fp64", "csize": c},
+        "config": headline_config(b.batch, world),
+        "launch": {"oracle": "CHESS-VEC (Alg. 7)", "csize": c, "points_per_step": int(statistics.median(pts))},
         "cpu_baseline": {"value": value, "unit": "HVP/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": f"each step: first {sample} of {b.batch} points, CHESS-VEC (Alg. 7) FP64, c={c}"},
+                         "sample": f"each step: the first {int(statistics.median(pts))} of {b.batch} points "
+                                   f"(about {per:.1f} s of work), CHESS-VEC (Alg. 7) FP64, c={c}"},
         "e2e": {"value": value, "unit": "HVP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+# ------------------------------------------------------------------ executed-instruction counts
+# The kernels whose executed FP instructions (and DRAM bytes) the roofline
+# reports: for each named workload and precision the symmetric HVP at every
+# chunk size the autotuner may pick, the plain method at the stated c = 4 of
+# Rosenbrock n=16, and the Hessians of Rosenbrock n=16 and n=256.  Counts are
+# per point: the per-point work of these kernels does not depend on the number
+# of points, threads per point or points per CTA, so a capture on a prefix of
+# the batch scales to the full batch by the number of points.
+PROFILE_BATCH = {("ackley_n64", 0): 16384, ("ackley_n64", 1): 16384, ("rosenbrock_n16", 0): 4096,
+                 ("rosenbrock_n16", 1): 4096, ("fletcher_powell_n32", 0): 2048, ("fletcher_powell_n32", 1): 8192,
+                 ("rosenbrock_n256", 0): 128, ("rosenbrock_n256", 1): 512}
+
+
+def profile_set():
+    from paper_2410_22575_gb300 import workloads as W
+
+    out = []
+    for name in ("ackley_n64", "rosenbrock_n16", "fletcher_powell_n32", "rosenbrock_n256"):
+        fn, n, _, _ = W.WORKLOADS[name]
+        for prec in (0, 1):
+            cs = [c for c in (2, 4, 8, 16) if c <= max(1, 1 << (n - 1).bit_length())]
+            for c in cs:
+                out.append((name, prec, "hvp", "symmetric", c))
+            if name == "rosenbrock_n16":
+                out.append((name, prec, "hvp", "plain", 4))
+            if name in ("rosenbrock_n16", "rosenbrock_n256"):
+                for c in cs:
+                    out.append((name, prec, "hessian", "symmetric", c))
+                out.append((name, prec, "hessian", "plain", 4))
+    return out
+
+
+def profile_kernels(args):
+    """Launch every kernel of profile_set() once on a prefix of its workload
+    (after one untimed warm-up launch of the library's FMA microbenchmark,
+    which no kernel filter matches).  Writes the launch order to
+    --profile-keys so --ingest-ncu can name the captured launches."""
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    cf.load()
+    keys = []
+    for name, prec, kind, method, c in profile_set():
+        b = W.workload(name, batch=PROFILE_BATCH[(name, prec)])
+        dt = torch.float64 if prec == 0 else torch.float32
+        if cf.chessfad_kernel_info(b.fn, prec, c, kind == "hvp")["local_bytes"] > 48:
+            continue
+        keep, params = [], None
+        if b.fn == W.FLETCHER_POWELL:
+            keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
+            params = cf.fp_params(*keep)
+        x = torch.tensor(b.x, dtype=dt, device="cuda")
+        v = torch.tensor(b.v, dtype=dt, device="cuda")
+        cfg = cf.Config(c, 1, 256, cf.PLAIN, 0) if method == "plain" else cf.Config(c, 0, 0, cf.SYMMETRIC, 0)
+        cfg = cf.chessfad_resolve_config(b.fn, b.n, b.batch, prec, cfg, hvp=(kind == "hvp"))
+        if kind == "hvp":
+            out = torch.empty_like(x)
+            st = cf.chessfad_hvp_config(b.fn, b.n, b.batch, cfg, x, v, out, params, prec)
+        else:
+            out = torch.empty((b.batch, b.n, b.n), dtype=dt, device="cuda")
+            st = cf.chessfad_hessian_config(b.fn, b.n, b.batch, cfg, x, out, params, prec)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise cf.ChessfadError(st, f"profile launch {name} {prec} {kind} {method} {c}")
+        keys.append({"key": count_key(name, prec, kind, method, c), "batch": b.batch, "fn": b.fn, "prec": prec,
+                     "c": c, "kind": kind, "method": method, "config": cfg.as_dict()})
+        del x, v, out, keep
+    with open(args.profile_keys, "w") as f:
+        json.dump({"source_hash": kernel_source_hash(), "launches": keys}, f, indent=1)
+    print(json.dumps({"mode": "profile-kernels", "launches": len(keys)}))
+
+
+NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,"
+               "smsp__sass_thread_inst_executed_op_ffma_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_fadd_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_dfma_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_dadd_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_dmul_pred_on.sum")
+
+
+def _num(s: str) -> float:
+    s = s.strip().replace(",", "")
+    return float(s) if s not in ("", "n/a") else float("nan")
+
+
+def read_ncu_csv(path: str) -> list[dict]:
+    """Launches of an ncu --csv capture (the details page, one row per
+    metric, or the raw page, one row per launch), in capture order."""
+    rows = list(csv.reader(open(path)))
+    hdr_i = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    hdr = rows[hdr_i]
+    body = rows[hdr_i + 1:]
+    launches: dict[str, dict] = {}
+    order = []
+    if "Metric Name" in hdr:
+        ci, ck, cm, cv, cu = (hdr.index(k) for k in ("ID", "Kernel Name", "Metric Name", "Metric Value",
+                                                     "Metric Unit"))
+        for r in body:
+            if len(r) <= cv:
+                continue
+            lid = r[ci]
+            if lid not in launches:
+                launches[lid] = {"name": r[ck]}
+                order.append(lid)
+            val = _num(r[cv])
+            unit = r[cu].strip().lower()
+            scale = {"kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9, "usecond": 1e3, "msecond": 1e6,
+                     "nsecond": 1.0, "second": 1e9}.get(unit, 1.0)
+            launches[lid][r[cm]] = val * scale
+    else:
+        ci, ck = hdr.index("ID"), hdr.index("Kernel Name")
+        for r in body:
+            if len(r) != len(hdr) or not r[ci].strip().isdigit():
+                continue
+            d = {"name": r[ck]}
+            for j, h in enumerate(hdr):
+                if "__" in h:
+                    d[h] = _num(r[j])
+            launches[r[ci]] = d
+            order.append(r[ci])
+    return [launches[i] for i in order]
+
+
+def ingest_ncu(args):
+    """profiles/counts.json from an ncu capture of --profile-kernels: per
+    kernel key, executed FP flops per point (2 x FMA + ADD + MUL thread
+    instructions, FP32 and FP64) and DRAM bytes per point."""
+    keys = json.load(open(args.profile_keys))
+    launches = [l for l in read_ncu_csv(args.ingest_ncu) if "sym_kernel" in l["name"] or "sweep_kernel" in l["name"]]
+    if len(launches) != len(keys["launches"]):
+        raise SystemExit(f"ncu captured {len(launches)} sweep launches, the profile run made {len(keys['launches'])}")
+    kernels = {}
+    for l, k in zip(launches, keys["launches"]):
+        nm = l["name"]
+        want_t = "double" if k["prec"] == 0 else "float"
+        base = "sweep_kernel" if k["method"] == "plain" else "sym_kernel"
+        targs = nm[nm.index("<") + 1:nm.index(">")].split(",")
+        targs = [t.strip() for t in targs]
+        if base not in nm or targs[0] != want_t or int(targs[2]) != k["c"] or int(targs[3]) != k["fn"] or \
+                int(targs[4]) != (1 if k["kind"] == "hvp" else 0):
+            raise SystemExit(f"launch {nm} does not match {k['key']}")
+        g = lambda m: l.get(f"smsp__sass_thread_inst_executed_op_{m}_pred_on.sum", 0.0)
+        fl = 2 * g("ffma") + g("fadd") + g("fmul") + 2 * g("dfma") + g("dadd") + g("dmul")
+        dram = l.get("dram__bytes_read.sum", float("nan")) + l.get("dram__bytes_write.sum", float("nan"))
+        u = k["batch"]
+        kernels[k["key"]] = {
+            "kernel": nm, "config": k["config"], "points_captured": u,
+            "executed_flops_per_unit": fl / u,
+            "fp32_flops_per_unit": (2 * g("ffma") + g("fadd") + g("fmul")) / u,
+            "fp64_flops_per_unit": (2 * g("dfma") + g("dadd") + g("dmul")) / u,
+            "dram_bytes_per_unit": None if math.isnan(dram) else dram / u,
+            "duration_ns_captured": l.get("gpu__time_duration.sum"),
+        }
+    doc = {"source_hash": keys["source_hash"],
+           "note": ("per point ('unit'): executed flops = 2 x FMA + ADD + MUL thread instructions (FP32 and "
+                    "FP64, predicated on), DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum, from one "
+                    "ncu capture per kernel on a prefix of the workload (points_captured), divided by the points"),
+           "command": args.ncu_command, "kernels": kernels}
+    if keys["source_hash"] != kernel_source_hash():
+        raise SystemExit("the kernel sources changed since the capture")
+    with open(COUNTS_FILE, "w") as f:
+        json.dump(doc, f, indent=1, sort_keys=True)
+    print(f"{len(kernels)} kernels -> {COUNTS_FILE}")
 
 
 def kernel_only(args):
@@ -641,6 +1080,7 @@ def report(args):
     from paper_2410_22575_gb300 import workloads as W
 
     rows = []
+    peaks = device_peaks(cf, 0)
 
     def timed(fn_call, reps):
         # device time per call: reps calls captured in one CUDA graph and
@@ -683,9 +1123,9 @@ def report(args):
             row = {"workload": name, "precision": "fp64" if prec == cf.FP64 else "fp32_comp",
                    "tuned": cfg.as_dict(), "hvp_per_s": b.batch / (t * 1e-3), "ms": t}
             mf = model_flops_hvp(b.fn, b.n, cfg.csize, cfg.method == cf.SYMMETRIC)
-            peak = SM_COUNT * (FP64_LANES_PER_SM if prec == cf.FP64 else FP32_LANES_PER_SM) * 2 * SM_MAX_MHZ * 1e6
             row["model_tflops"] = mf * b.batch / (t * 1e-3) / 1e12
-            row["frac_of_derived_peak"] = mf * b.batch / (t * 1e-3) / peak
+            peak = peaks[PREC_NAME[prec]]["microbench"]
+            row["model_frac_of_microbench"] = None if not peak else mf * b.batch / (t * 1e-3) / peak
             c0 = 4 if name == "rosenbrock_n16" else cfg.csize
             plain = cf.Config(c0, 1, 256)
             t = timed(lambda: cf.chessfad_hvp_config(b.fn, b.n, b.batch, plain, x, v, out, params, prec), reps)
@@ -791,12 +1231,15 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--impl", choices=["chessfad", "reference"], default="chessfad")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ragged", action="store_true", help="skip the 100000-request uneven batch")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the other named workloads")
+    ap.add_argument("--workload-steps", type=int, default=5, help="timed steps per row of the workloads block")
     ap.add_argument("--ragged-steps", type=int, default=1)
+    ap.add_argument("--ragged-cpu-cap", type=float, default=3e9,
+                    help="uneven-batch CPU baseline: model-flop cap of the sampled requests")
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
     ap.add_argument("--ragged-only", action="store_true",
                     help="run only the uneven-batch kernel on a subset of the 100000-request workload (for ncu)")
@@ -807,6 +1250,12 @@ def main():
     ap.add_argument("--report", action="store_true", help="per-workload table (all named workloads)")
     ap.add_argument("--chunk-study", action="store_true", help="measured best chunk size vs the Sec. V model")
     ap.add_argument("--cpu-report", action="store_true", help="CPU-baseline leg for every named workload")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="launch each kernel of the executed-count set once (the command ncu captures)")
+    ap.add_argument("--profile-keys", default="profile_keys.json",
+                    help="where --profile-kernels writes, and --ingest-ncu reads, the launch order")
+    ap.add_argument("--ingest-ncu", default=None, help="ncu CSV of --profile-kernels -> profiles/counts.json")
+    ap.add_argument("--ncu-command", default="", help="the ncu command recorded in profiles/counts.json")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fn", type=int, default=None, help="kernel-only: function id instead of a named workload")
     ap.add_argument("--n", type=int, default=64)
@@ -816,16 +1265,20 @@ def main():
     ap.add_argument("--csize", type=int, default=32)
     ap.add_argument("--tpr", type=int, default=1)
     ap.add_argument("--block", type=int, default=128)
-    ap.add_argument("--ref-budget", type=float, default=150.0,
+    ap.add_argument("--ref-budget", type=float, default=100.0,
                     help="reference arm: seconds of oracle work over all steps (bounded per step)")
     ap.add_argument("--e2e-slices", type=int, default=16,
                     help="slices of the end-to-end call (copies of one overlap the sweep of the next)")
     ap.add_argument("--method", choices=["plain", "symmetric", "symmetric_sparse"], default="plain")
     ap.add_argument("--tpp", type=int, default=64, help="kernel-only, symmetric: threads per point")
     args = ap.parse_args()
-    if args.warmup < 3 and not args.kernel_only:
+    if args.warmup < 3 and not (args.kernel_only or args.profile_kernels or args.ragged_only):
         args.warmup = 3
-    if args.cpu_report:
+    if args.ingest_ncu:
+        ingest_ncu(args)
+    elif args.profile_kernels:
+        profile_kernels(args)
+    elif args.cpu_report:
         cpu_baseline_report(args)
     elif args.chunk_study:
         chunk_study(args)

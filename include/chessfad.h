@@ -131,9 +131,15 @@ typedef struct {
  *   threads_per_point symmetric method: threads sharing one point's
  *                     (row, chunk) items, 8..256 power of two (below 32 a
  *                     warp serves several points)
- * Zero in any field means "default"; with csize 0, method 0 also means the
- * default (tuned, else chessfad_default_config) method, otherwise method 0 is
- * the plain method.  The
+ * Zero in any field means "default".  With csize 0, method 0 means the
+ * default method (the tuned one, else chessfad_default_config's), not
+ * necessarily the plain method, and the chunk size follows the method: the
+ * tuned or default configuration's for that method, else the Sec. V optimum
+ * c = sqrt(n/2) (rounded up to a power of two) for the symmetric methods and
+ * the largest register-resident chunk for the plain and one-thread-per-point
+ * methods; with csize != 0, method 0 is the plain method.  Default
+ * threads_per_point never exceeds the point's (row, chunk) item count
+ * C nch (nch + 1) / 2 rounded up to a power of two (at least 8).  The
  * symmetric HVP stages a point's chunks on and above the diagonal chunks in
  * shared memory (about n (n + C) / 2 values per point) and sums whole rows,
  * reproducibly, for n up to about 280 (FP32) / 200 (FP64); beyond, it sums
@@ -208,6 +214,13 @@ CHESSFAD_API int chessfad_hvp_host(int fn, int n, long long batch, int csize, co
  * with that chunk size.  Host only; launches nothing. */
 CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_config *cfg);
 
+/* The configuration chessfad_hvp_config (hvp != 0) or
+ * chessfad_hessian_config (hvp == 0) would use for (fn, n, batch, prec, cfg)
+ * (cfg may be NULL), with every default filled in, or the error it would
+ * return for cfg.  Host only; launches nothing. */
+CHESSFAD_API int chessfad_resolve_config(int fn, int n, long long batch, int prec, int hvp,
+                                         const chessfad_config *cfg, chessfad_config *out);
+
 /* Autotune the HVP launch configuration for (fn, n, prec) by timing the
  * candidates on the caller's buffers (x, v, out as for chessfad_hvp; out is
  * overwritten): for every chunk size (largest first, following the Sec. V
@@ -216,17 +229,34 @@ CHESSFAD_API int chessfad_default_config(int fn, int n, long long batch, int pre
  * block_threads), discarding chunk sizes whose kernels spill registers.  The
  * seed-sparse and one-thread-per-point methods are never candidates.  The
  * winner is stored in the process-wide table used by
- * csize = 0 and returned in *best (may be NULL).  Synchronises `stream`.
- * Allocates no device memory. */
+ * csize = 0 (chessfad_hvp) and returned in *best (may be NULL).
+ * Synchronises `stream`.  Allocates no device memory. */
 CHESSFAD_API int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,
                           const chessfad_fp_params *params, int prec, chessfad_stream_t stream,
                           chessfad_config *best);
 
-/* Peak CUDA-core throughput measured on the current device by a dependent-
- * chain FMA microbenchmark over all SMs: FP32 FFMA for CHESSFAD_FP32_COMP,
+/* Autotune the Hessian launch configuration for (fn, n, prec) as
+ * chessfad_autotune_hvp does for the HVP (the same candidates, timed as
+ * Hessian launches on a prefix of the caller's x and H, which is
+ * overwritten).  The winner is stored in the process-wide Hessian table used
+ * by chessfad_hessian with csize = 0 and returned in *best (may be NULL).
+ * Synchronises `stream`; allocates no device memory. */
+CHESSFAD_API int chessfad_autotune_hessian(int fn, int n, long long batch, const void *x, void *H,
+                                           const chessfad_fp_params *params, int prec, chessfad_stream_t stream,
+                                           chessfad_config *best);
+
+/* Peak CUDA-core throughput measured on the current device by an
+ * independent-chain FMA microbenchmark over all SMs: FP32 FFMA for CHESSFAD_FP32_COMP,
  * FP64 DFMA for CHESSFAD_FP64, counting one FMA as two flops.  Synchronises
  * the device; allocates no device memory. */
 CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s);
+
+/* chessfad_peak_flops, plus the SM clock (MHz) the fastest run saw, read
+ * from the SM cycle counter against the GPU's nanosecond timer inside the
+ * kernel (sm_mhz may be NULL).  The FP32 shapes timed are 8 chains x 8 CTAs
+ * and 16 chains x 4 CTAs of 256 threads per SM; FP64 adds 16 and 32 chains,
+ * at 8 and 4 CTAs per SM; the best is reported. */
+CHESSFAD_API int chessfad_peak_info(int prec, double *flops_per_s, double *sm_mhz);
 
 /* ---------------------------------------------------------------------------
  * Uneven batches: requests of different functions and sizes in one launch.
@@ -300,9 +330,11 @@ CHESSFAD_API int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpac
  * The scratch (the plan's tables, counters and accumulators) lives in a
  * static device array of CHESSFAD_RAGGED_STATIC_BYTES that every GPU which
  * loads the library holds until the process exits.  Each call copies the
- * plan's tables into it (cudaMemcpyAsync on stream), zeroes the counters and
- * accumulators (cudaMemsetAsync) and launches the persistent kernel; it
- * allocates nothing and calls no allocating routine.
+ * plan's tables into it from the plan's host memory (cudaMemcpyAsync on
+ * stream), zeroes the counters and accumulators (cudaMemsetAsync) and
+ * launches the persistent kernel; it allocates nothing and calls no
+ * allocating routine.  Keep the plan alive for as long as any work issued by
+ * a call with it may still run.
  * The first call on a device also looks up the array's device address on
  * that device (cudaGetSymbolAddress); make that first call before any stream
  * capture.  All calls share the one array, so calls whose work overlaps on

@@ -80,8 +80,11 @@ def load(build_if_missing: bool = True):
         lib.chessfad_hvp_config.argtypes = [I, I, L, P, P, P, P, P, I, P]
         lib.chessfad_hessian_config.argtypes = [I, I, L, P, P, P, P, I, P]
         lib.chessfad_default_config.argtypes = [I, I, L, I, P]
+        lib.chessfad_resolve_config.argtypes = [I, I, L, I, I, P, P]
+        lib.chessfad_autotune_hessian.argtypes = [I, I, L, P, P, P, I, P, P]
         lib.chessfad_autotune_hvp.argtypes = [I, I, L, P, P, P, P, I, P, P]
         lib.chessfad_peak_flops.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+        lib.chessfad_peak_info.argtypes = [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         lib.chessfad_kernel_info.argtypes = [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(L)]
         lib.chessfad_ragged_plan_create.argtypes = [P, L, I, I, ctypes.POINTER(P)]
         lib.chessfad_ragged_plan_destroy.argtypes = [P]
@@ -110,7 +113,9 @@ def load(build_if_missing: bool = True):
         lib.chessfad_strerror.restype = ctypes.c_char_p
         lib.chessfad_version.argtypes = []
         for name in ("chessfad_hvp", "chessfad_hessian", "chessfad_hvp_config", "chessfad_hessian_config",
-                     "chessfad_default_config", "chessfad_autotune_hvp", "chessfad_peak_flops",
+                     "chessfad_default_config", "chessfad_resolve_config", "chessfad_autotune_hvp",
+                     "chessfad_autotune_hessian", "chessfad_peak_flops",
+                     "chessfad_peak_info",
                      "chessfad_kernel_info", "chessfad_version", "chessfad_ragged_plan_create",
                      "chessfad_ragged_plan_destroy", "chessfad_ragged_plan_info", "chessfad_ragged_plan_upload",
                      "chessfad_hvp_ragged"):
@@ -193,6 +198,22 @@ def chessfad_default_config(fn, n, batch, prec) -> Config:
     return cfg
 
 
+def chessfad_resolve_config(fn, n, batch, prec, cfg: Config | None = None, hvp: bool = True) -> Config:
+    out = Config()
+    _check(load().chessfad_resolve_config(fn, n, batch, prec, 1 if hvp else 0,
+                                          ctypes.byref(cfg) if cfg is not None else None, ctypes.byref(out)),
+           "chessfad_resolve_config")
+    return out
+
+
+def chessfad_autotune_hessian(fn, n, batch, x, H, params=None, prec=FP64, stream=None) -> Config:
+    cfg = Config()
+    p = ctypes.byref(params) if params is not None else None
+    _check(load().chessfad_autotune_hessian(fn, n, batch, _addr(x), _addr(H), p, prec, _stream(stream),
+                                            ctypes.byref(cfg)), "chessfad_autotune_hessian")
+    return cfg
+
+
 def chessfad_autotune_hvp(fn, n, batch, x, v, out, params=None, prec=FP64, stream=None) -> Config:
     cfg = Config()
     p = ctypes.byref(params) if params is not None else None
@@ -205,6 +226,14 @@ def chessfad_peak_flops(prec) -> float:
     f = ctypes.c_double()
     _check(load().chessfad_peak_flops(prec, ctypes.byref(f)), "chessfad_peak_flops")
     return f.value
+
+
+def chessfad_peak_info(prec) -> tuple[float, float]:
+    """(FMA peak flop/s, SM clock in MHz the fastest run saw)."""
+    f = ctypes.c_double()
+    mhz = ctypes.c_double()
+    _check(load().chessfad_peak_info(prec, ctypes.byref(f), ctypes.byref(mhz)), "chessfad_peak_info")
+    return f.value, mhz.value
 
 
 def chessfad_kernel_info(fn, prec, csize, hvp=True) -> dict:

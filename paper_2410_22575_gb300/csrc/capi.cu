@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -30,70 +31,115 @@ static constexpr size_t kMaxFrameNoSpill = 48;
 
 static bool valid_chunk(int c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16 || c == 32; }
 
-// Tuned configurations keyed by (fn, n, prec).
+// Tuned configurations keyed by (fn, n, prec): HVPs and Hessians.
 static std::mutex g_mu;
 static std::map<std::tuple<int, int, int>, chessfad_config> g_table;
+static std::map<std::tuple<int, int, int>, chessfad_config> g_htable;
 
-// Default: the largest chunk that keeps the hDual state comfortably in
-// registers (the plain method's multiplication count (6 + 3/c) n^2 M falls
-// with c, Sec. V), one chunk per lane where a row has <= 32 chunks.
-// Rows (point, i) that fill the GPU several times over with one thread each.
-static constexpr long long kRowsOneLane = 4LL * 152 * 256;
+// Multiprocessors of the current device (queried once per device; 152 on
+// GB300 when the query fails, e.g. with no device).
+static int device_sms()
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    int s = cache[dev].load(std::memory_order_relaxed);
+    if (s > 0) return s;
+    if (cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || s <= 0) return 152;
+    cache[dev].store(s, std::memory_order_relaxed);
+    return s;
+}
 
-static int default_threads_per_point(int n, long long batch);
+// Threads that fill the GPU several times over: four 256-thread CTAs per
+// multiprocessor.
+static long long rows_one_lane() { return 4LL * device_sms() * 256; }
+
+static int default_threads_per_point(int n, int csize, long long batch);
+
+// Largest chunk that keeps the plain method's hDual state comfortably in
+// registers (its multiplication count (6 + 3/c) n^2 M falls with c, Sec. V).
+static int plain_chunk(int fn, int n, int prec)
+{
+    int cmax = (prec == CHESSFAD_FP64) ? 8 : 16;
+    if (fn == CHESSFAD_FLETCHER_POWELL) cmax = (prec == CHESSFAD_FP64) ? 4 : 16;
+    return std::min(cmax, next_pow2(n));
+}
+
+// The symmetric method's chunk: the Sec. V optimum c = sqrt(n/2), rounded up
+// to a power of two, within the plain method's register budget.
+static int sym_chunk(int fn, int n, int prec)
+{
+    return std::min(plain_chunk(fn, n, prec), next_pow2((int)std::ceil(std::sqrt(n / 2.0))));
+}
 
 static chessfad_config default_config(int fn, int n, long long batch, int prec)
 {
     chessfad_config c{};
-    int cmax = (prec == CHESSFAD_FP64) ? 8 : 16;
-    if (fn == CHESSFAD_FLETCHER_POWELL) cmax = (prec == CHESSFAD_FP64) ? 4 : 16;
-    c.csize = std::min(cmax, next_pow2(n));
+    c.csize = plain_chunk(fn, n, prec);
     const int nch = (n + c.csize - 1) / c.csize;
     // Enough rows: one thread per row sweeps all of the row's chunks (the
     // per-point prologue is amortised over the most work).  Few rows: spread
     // a row's chunks over lanes (the paper's L2) to fill the GPU.
     int tpr = 1;
     const long long rows = batch * (long long)n;
-    while (tpr < 32 && tpr < nch && rows * tpr < kRowsOneLane) tpr <<= 1;
+    while (tpr < 32 && tpr < nch && rows * tpr < rows_one_lane()) tpr <<= 1;
     c.threads_per_row = tpr;
     c.block_threads = 256;
     c.method = CHESSFAD_METHOD_PLAIN;
-    c.threads_per_point = default_threads_per_point(n, batch);
+    c.threads_per_point = default_threads_per_point(n, sym_chunk(fn, n, prec), batch);
     if (n >= 4) {
         // The symmetric method (about half the evaluations) at the Sec. V
         // optimum c = sqrt(n/2), rounded up to a power of two.
         c.method = CHESSFAD_METHOD_SYMMETRIC;
-        c.csize = std::min(cmax, next_pow2((int)std::ceil(std::sqrt(n / 2.0))));
+        c.csize = sym_chunk(fn, n, prec);
         c.block_threads = std::max(128, c.threads_per_point);
     }
     return c;
 }
 
-static chessfad_config resolve(int fn, int n, long long batch, int prec, const chessfad_config *cfg, int csize_hint)
+static chessfad_config resolve(int fn, int n, long long batch, int prec, const chessfad_config *cfg, int csize_hint,
+                               bool hvp)
 {
     chessfad_config c{};
     if (cfg) c = *cfg;
     if (c.csize == 0 && csize_hint != 0) c.csize = csize_hint;
     if (c.csize == 0) {
-        std::lock_guard<std::mutex> lk(g_mu);
-        auto it = g_table.find(std::make_tuple(fn, n, prec));
-        chessfad_config base = (it != g_table.end()) ? it->second : default_config(fn, n, batch, prec);
-        if (c.threads_per_row == 0) c.threads_per_row = base.threads_per_row;
-        if (c.block_threads == 0) c.block_threads = base.block_threads;
-        if (c.threads_per_point == 0) c.threads_per_point = base.threads_per_point;
+        chessfad_config base;
+        bool tuned = false;
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            const auto &table = hvp ? g_table : g_htable;
+            auto it = table.find(std::make_tuple(fn, n, prec));
+            tuned = it != table.end();
+            base = tuned ? it->second : default_config(fn, n, batch, prec);
+        }
+        // Method 0 with csize 0 is "the default method" (the tuned one, else
+        // the default configuration's), not necessarily the plain method.
         if (!cfg || cfg->method == 0) c.method = base.method;
-        c.csize = base.csize;
+        if (c.method == base.method) {
+            c.csize = base.csize;
+            if (c.threads_per_row == 0) c.threads_per_row = base.threads_per_row;
+            if (c.block_threads == 0) c.block_threads = base.block_threads;
+            if (c.threads_per_point == 0) c.threads_per_point = base.threads_per_point;
+        } else if (c.method == CHESSFAD_METHOD_SYMMETRIC || c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE) {
+            c.csize = sym_chunk(fn, n, prec);
+        } else {
+            c.csize = plain_chunk(fn, n, prec);
+        }
         // the seed-sparse kernels exist for chunk sizes 4, 8 and 16 only, the
         // one-thread-per-point kernels for 1 .. 16
         if (c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE) c.csize = std::min(16, std::max(4, c.csize));
         if (c.method == CHESSFAD_METHOD_POINT) c.csize = std::min(16, c.csize);
     }
-    if (c.threads_per_point == 0) c.threads_per_point = default_threads_per_point(n, batch);
+    if (c.threads_per_point == 0) c.threads_per_point = default_threads_per_point(n, c.csize, batch);
     if (c.threads_per_row == 0 || c.block_threads == 0) {
         chessfad_config d = default_config(fn, n, batch, prec);
         const int nch = (n + c.csize - 1) / c.csize;
         if (c.threads_per_row == 0) c.threads_per_row = std::min(d.threads_per_row, std::max(1, next_pow2(nch)));
-        if (c.block_threads == 0) c.block_threads = d.block_threads;
+        if (c.block_threads == 0) {
+            const bool sym = c.method == CHESSFAD_METHOD_SYMMETRIC || c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE;
+            c.block_threads = sym ? std::max(128, c.threads_per_point) : d.block_threads;
+        }
     }
     return c;
 }
@@ -127,12 +173,18 @@ static int check_config(const chessfad_config &c)
     return CHESSFAD_SUCCESS;
 }
 
-// Symmetric method: threads per point that fill the GPU several times over.
-static int default_threads_per_point(int n, long long batch)
+// Symmetric method: threads per point that fill the GPU several times over,
+// but no more than the point has (row, chunk) items (C nch (nch+1) / 2),
+// rounded up to a power of two, at least 8: a small point leaves no lanes
+// idle for want of items.
+static int default_threads_per_point(int n, int csize, long long batch)
 {
-    (void)n;
-    int p = 32;
-    while (p < 256 && batch * (long long)p < kRowsOneLane) p <<= 1;
+    const long long nch = (n + csize - 1) / csize;
+    const long long items = (long long)csize * nch * (nch + 1) / 2;
+    int cap = 8;
+    while (cap < 256 && cap < items) cap <<= 1;
+    int p = std::min(32, cap);
+    while (p < cap && batch * (long long)p < rows_one_lane()) p <<= 1;
     return p;
 }
 
@@ -288,12 +340,93 @@ static int run(int fn, int n, long long batch, const chessfad_config *cfg, int c
     if (st) return st;
     if (csize_hint != 0 && !valid_chunk(csize_hint)) return CHESSFAD_ERR_CHUNK;
     if (cfg && cfg->csize != 0 && !valid_chunk(cfg->csize)) return CHESSFAD_ERR_CHUNK;
-    const chessfad_config c = resolve(fn, n, batch, prec, cfg, csize_hint);
+    const chessfad_config c = resolve(fn, n, batch, prec, cfg, csize_hint, hvp);
     st = check_config(c);
     if (st) return st;
     if (batch == 0) return CHESSFAD_SUCCESS;
     if (!x || !out || (hvp && !v)) return CHESSFAD_ERR_NULL;
     return launch(fn, n, batch, c, x, v, out, params, prec, hvp, stream);
+}
+
+// The autotuner of chessfad_autotune_hvp / chessfad_autotune_hessian: times
+// every candidate on a prefix of the caller's batch and stores the fastest in
+// the HVP or the Hessian table.
+static int autotune(int fn, int n, long long batch, const void *x, const void *v, void *out,
+                    const chessfad_fp_params *params, int prec, cudaStream_t stream, bool hvp, chessfad_config *best)
+{
+    int st = check_common(fn, n, batch, prec, params);
+    if (st) return st;
+    if (batch == 0) return CHESSFAD_ERR_BATCH;
+    if (!x || !out || (hvp && !v)) return CHESSFAD_ERR_NULL;
+
+    // Candidate chunk sizes: powers of two up to next_pow2(n), ordered by the
+    // Sec. V model of the plain method, whose multiplication count
+    // (6 + 3/c) n^2 M falls with c, so large chunks are tried first.
+    std::vector<int> chunks;
+    for (int c = std::min(32, next_pow2(n)); c >= 1; c >>= 1) chunks.push_back(c);
+
+    // Time on a prefix of the batch big enough to fill the GPU several times.
+    const long long want_threads = 2 * rows_one_lane();
+    long long sub = std::min<long long>(batch, std::max<long long>(1, want_threads / n));
+
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CHESSFAD_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CHESSFAD_ERR_CUDA;
+    }
+    chessfad_config win{};
+    float win_ms = INFINITY;
+    int rc = CHESSFAD_SUCCESS;
+    // Candidates: plain method over (threads/row, CTA size), symmetric method
+    // (Alg. 6 / Alg. 8) over threads/point; kernels that spill are skipped.
+    std::vector<chessfad_config> cands;
+    for (int c : chunks) {
+        cudaFuncAttributes fa{};
+        if (kernel_attr(fn, prec, c, hvp, &fa) != cudaSuccess || fa.localSizeBytes > kMaxFrameNoSpill) continue;
+        const int nch = (n + c - 1) / c;
+        const int tmax = std::min(32, next_pow2(nch));
+        for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
+            for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
+        if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
+        // threads per point: 8 for small n (few items per point), 256 for
+        // large n; never more than twice the point's items
+        const long long items = (long long)c * nch * (nch + 1) / 2;
+        for (int p : {8, 16, 32, 64, 128, 256})
+            for (int bt : {128, 256})
+                if (bt >= p && (p < 256 || n >= 128) && (p > 8 || n <= 32) && (p <= 8 || p < 2 * items))
+                    cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
+    }
+    for (const chessfad_config &cfg : cands) {
+        if (launch(fn, n, sub, cfg, x, v, out, params, prec, hvp, stream) != CHESSFAD_SUCCESS) {
+            cudaGetLastError();
+            continue;  // e.g. a symmetric HVP whose staged chunks exceed shared memory
+        }
+        cudaEventRecord(e0, stream);
+        const int reps = 3;
+        for (int k = 0; k < reps; ++k) launch(fn, n, sub, cfg, x, v, out, params, prec, hvp, stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = CHESSFAD_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < win_ms) {
+            win_ms = ms;
+            win = cfg;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (!std::isfinite(win_ms)) return CHESSFAD_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        (hvp ? g_table : g_htable)[std::make_tuple(fn, n, prec)] = win;
+    }
+    if (best) *best = win;
+    return CHESSFAD_SUCCESS;
 }
 
 }  // namespace chessfad
@@ -333,86 +466,37 @@ int chessfad_default_config(int fn, int n, long long batch, int prec, chessfad_c
     if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
     if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
     if (batch < 0) return CHESSFAD_ERR_BATCH;
-    *cfg = resolve(fn, n, batch, prec, nullptr, 0);
+    *cfg = resolve(fn, n, batch, prec, nullptr, 0, true);
+    return CHESSFAD_SUCCESS;
+}
+
+int chessfad_resolve_config(int fn, int n, long long batch, int prec, int hvp, const chessfad_config *cfg,
+                            chessfad_config *out)
+{
+    if (!out) return CHESSFAD_ERR_NULL;
+    if (fn < 0 || fn > 2) return CHESSFAD_ERR_FUNCTION;
+    if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
+    if (n < 1 || n > CHESSFAD_MAX_N) return CHESSFAD_ERR_SIZE;
+    if (batch < 0) return CHESSFAD_ERR_BATCH;
+    if (cfg && cfg->csize != 0 && !valid_chunk(cfg->csize)) return CHESSFAD_ERR_CHUNK;
+    const chessfad_config c = resolve(fn, n, batch, prec, cfg, 0, hvp != 0);
+    const int st = check_config(c);
+    if (st) return st;
+    *out = c;
     return CHESSFAD_SUCCESS;
 }
 
 int chessfad_autotune_hvp(int fn, int n, long long batch, const void *x, const void *v, void *out,
-                          const chessfad_fp_params *params, int prec, chessfad_stream_t stream_,
+                          const chessfad_fp_params *params, int prec, chessfad_stream_t stream,
                           chessfad_config *best)
 {
-    cudaStream_t stream = (cudaStream_t)stream_;
-    int st = check_common(fn, n, batch, prec, params);
-    if (st) return st;
-    if (batch == 0) return CHESSFAD_ERR_BATCH;
-    if (!x || !v || !out) return CHESSFAD_ERR_NULL;
+    return autotune(fn, n, batch, x, v, out, params, prec, (cudaStream_t)stream, true, best);
+}
 
-    // Candidate chunk sizes: powers of two up to next_pow2(n), ordered by the
-    // Sec. V model of the plain method, whose multiplication count
-    // (6 + 3/c) n^2 M falls with c, so large chunks are tried first.
-    std::vector<int> chunks;
-    for (int c = std::min(32, next_pow2(n)); c >= 1; c >>= 1) chunks.push_back(c);
-
-    // Time on a prefix of the batch big enough to fill the GPU several times.
-    const long long want_threads = 8LL * 152 * 256;
-    long long sub = std::min<long long>(batch, std::max<long long>(1, want_threads / n));
-
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return CHESSFAD_ERR_CUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return CHESSFAD_ERR_CUDA;
-    }
-    chessfad_config win{};
-    float win_ms = INFINITY;
-    int rc = CHESSFAD_SUCCESS;
-    // Candidates: plain method over (threads/row, CTA size), symmetric method
-    // (Alg. 8) over threads/point; kernels that spill are skipped.
-    std::vector<chessfad_config> cands;
-    for (int c : chunks) {
-        cudaFuncAttributes fa{};
-        if (kernel_attr(fn, prec, c, true, &fa) != cudaSuccess || fa.localSizeBytes > kMaxFrameNoSpill) continue;
-        const int nch = (n + c - 1) / c;
-        const int tmax = std::min(32, next_pow2(nch));
-        for (int t = tmax; t >= std::max(1, tmax / 8); t >>= 1)
-            for (int bt : {256, 128}) cands.push_back(chessfad_config{c, t, bt, CHESSFAD_METHOD_PLAIN, 32});
-        if (std::max(1, tmax / 8) > 1) cands.push_back(chessfad_config{c, 1, 256, CHESSFAD_METHOD_PLAIN, 32});
-        // threads per point: 8 for small n (few items per point), 256 for large n
-        for (int p : {8, 16, 32, 64, 128, 256})
-            for (int bt : {128, 256})
-                if (bt >= p && (p < 256 || n >= 128) && (p > 8 || n <= 32))
-                    cands.push_back(chessfad_config{c, 1, bt, CHESSFAD_METHOD_SYMMETRIC, p});
-    }
-    for (const chessfad_config &cfg : cands) {
-        if (launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream) != CHESSFAD_SUCCESS) {
-            cudaGetLastError();
-            continue;  // e.g. a symmetric HVP whose staged chunks exceed shared memory
-        }
-        cudaEventRecord(e0, stream);
-        const int reps = 3;
-        for (int k = 0; k < reps; ++k) launch(fn, n, sub, cfg, x, v, out, params, prec, true, stream);
-        cudaEventRecord(e1, stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = CHESSFAD_ERR_CUDA;
-            break;
-        }
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < win_ms) {
-            win_ms = ms;
-            win = cfg;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (rc) return rc;
-    if (!std::isfinite(win_ms)) return CHESSFAD_ERR_CUDA;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        g_table[std::make_tuple(fn, n, prec)] = win;
-    }
-    if (best) *best = win;
-    return CHESSFAD_SUCCESS;
+int chessfad_autotune_hessian(int fn, int n, long long batch, const void *x, void *H, const chessfad_fp_params *params,
+                              int prec, chessfad_stream_t stream, chessfad_config *best)
+{
+    return autotune(fn, n, batch, x, nullptr, H, params, prec, (cudaStream_t)stream, false, best);
 }
 
 int chessfad_kernel_info(int fn, int prec, int csize, int hvp, int *registers, long long *local_bytes)

@@ -1,8 +1,12 @@
 // peak.cu -- CUDA-core FMA peak microbenchmark (the roofline denominator of
 // the ALU-bound sweep kernels).  Every thread runs NCH independent dependent
-// chains a = fma(a, m, b) over all SMs at full occupancy; one FMA counts as
-// two flops.  The result is folded into a never-taken store so the chains
-// cannot be removed.
+// chains a = fma(a, m, b) over all SMs; one FMA counts as two flops.  The
+// result is folded into a never-taken store so the chains cannot be removed.
+// Several (chains per thread, CTAs per SM) shapes are timed and the best is
+// reported, so the number is the pipe's throughput rather than one shape's
+// latency or occupancy limit.  Thread 0 of CTA 0 reads the SM cycle counter
+// and the global nanosecond timer around its loop, which gives the SM clock
+// the run actually saw.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -14,9 +18,24 @@ namespace chessfad {
 template <typename T>
 __device__ T g_peak_sink;
 
+__device__ unsigned long long g_peak_clk[2];
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 template <typename T, int NCH>
 __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T seed)
 {
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long c0 = 0, t0 = 0;
+    if (timer) {
+        t0 = global_ns();
+        c0 = clock64();
+    }
     T a[NCH];
 #pragma unroll
     for (int c = 0; c < NCH; ++c) a[c] = seed + T(c) * T(1e-3) + T(threadIdx.x) * T(1e-7);
@@ -32,15 +51,26 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T seed)
 #pragma unroll
     for (int c = 0; c < NCH; ++c) s += a[c];
     if (s == T(-12345.0)) g_peak_sink<T> = s;
+    if (timer) {
+        const unsigned long long c1 = clock64();
+        const unsigned long long t1 = global_ns();
+        g_peak_clk[0] = c1 - c0;
+        g_peak_clk[1] = t1 - t0;
+    }
 }
 
+struct PeakResult {
+    double flops = 0.0;
+    double sm_mhz = 0.0;
+};
+
 template <typename T, int NCH>
-static int measure(int iters, double *flops)
+static int measure(int iters, int blocks_per_sm, PeakResult *best)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
-    const int threads = 256, blocks = sms * 8;
+    const int threads = 256, blocks = sms * blocks_per_sm;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return CHESSFAD_ERR_CUDA;
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -48,7 +78,6 @@ static int measure(int iters, double *flops)
         return CHESSFAD_ERR_CUDA;
     }
     fma_peak_kernel<T, NCH><<<blocks, threads>>>(std::max(1, iters / 16), T(1));
-    double best = 0.0;
     int rc = CHESSFAD_SUCCESS;
     for (int rep = 0; rep < 3 && rc == CHESSFAD_SUCCESS; ++rep) {
         cudaEventRecord(e0);
@@ -60,13 +89,40 @@ static int measure(int iters, double *flops)
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
+        unsigned long long clk[2] = {0, 0};
+        if (cudaMemcpyFromSymbol(clk, g_peak_clk, sizeof(clk)) != cudaSuccess) {
+            rc = CHESSFAD_ERR_CUDA;
+            break;
+        }
         const double fl = 2.0 * NCH * 16.0 * (double)iters * (double)blocks * threads;
-        best = std::max(best, fl / (ms * 1e-3));
+        const double f = fl / (ms * 1e-3);
+        if (f > best->flops) {
+            best->flops = f;
+            best->sm_mhz = clk[1] ? (double)clk[0] / (double)clk[1] * 1e3 : 0.0;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == CHESSFAD_SUCCESS) *flops = best;
     return rc;
+}
+
+static int peak(int prec, PeakResult *r)
+{
+    int rc;
+    if (prec == CHESSFAD_FP32_COMP) {
+        // FP32: 128 lanes per SM; 8 chains at 8 CTAs of 256 per SM saturate.
+        if ((rc = measure<float, 8>(40000, 8, r))) return rc;
+        return measure<float, 16>(20000, 4, r);
+    }
+    if (prec == CHESSFAD_FP64) {
+        // FP64: few lanes per SM and a long pipe: more chains per thread, and
+        // both full and half occupancy, to reach the pipe's throughput.
+        if ((rc = measure<double, 8>(800, 8, r))) return rc;
+        if ((rc = measure<double, 16>(400, 8, r))) return rc;
+        if ((rc = measure<double, 16>(800, 4, r))) return rc;
+        return measure<double, 32>(400, 4, r);
+    }
+    return CHESSFAD_ERR_PRECISION;
 }
 
 }  // namespace chessfad
@@ -74,7 +130,20 @@ static int measure(int iters, double *flops)
 extern "C" CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s)
 {
     if (!flops_per_s) return CHESSFAD_ERR_NULL;
-    if (prec == CHESSFAD_FP32_COMP) return chessfad::measure<float, 8>(40000, flops_per_s);
-    if (prec == CHESSFAD_FP64) return chessfad::measure<double, 8>(800, flops_per_s);
-    return CHESSFAD_ERR_PRECISION;
+    chessfad::PeakResult r;
+    const int rc = chessfad::peak(prec, &r);
+    if (rc == CHESSFAD_SUCCESS) *flops_per_s = r.flops;
+    return rc;
+}
+
+extern "C" CHESSFAD_API int chessfad_peak_info(int prec, double *flops_per_s, double *sm_mhz)
+{
+    if (!flops_per_s) return CHESSFAD_ERR_NULL;
+    chessfad::PeakResult r;
+    const int rc = chessfad::peak(prec, &r);
+    if (rc == CHESSFAD_SUCCESS) {
+        *flops_per_s = r.flops;
+        if (sm_mhz) *sm_mhz = r.sm_mhz;
+    }
+    return rc;
 }

@@ -92,7 +92,7 @@ cudaError_t launch_point(SweepArgs a, cudaStream_t stream)
 {
     const size_t bytes = point_smem_bytes<T, IO, C, FN, HVP, MB>(a);
     auto kern = point_kernel<T, IO, C, FN, HVP, MB>;
-    static int configured[64] = {0};
+    static std::atomic<int> configured[64];
     cudaError_t e = opt_in_smem(kern, bytes, configured);
     if (e != cudaSuccess) return e;
     const long long blocks = (a.batch + a.maxpts - 1) / a.maxpts;

@@ -224,6 +224,9 @@ struct chessfad_ragged_plan_s {
     size_t off_tiles = 0, off_list = 0, off_offs = 0, off_eoffs = 0, off_soffs = 0, off_counter = 0, off_done = 0,
            off_acc = 0, table_bytes = 0, total = 0;
     std::vector<unsigned char> image;  // host image of the tables (table_bytes)
+    // persistent grid size, computed for the device of the first run (and
+    // again when a run is on another device); guarded by mu
+    std::mutex mu;
     int grid_dev = -1, grid = 0;
     double est_cost = 0.0;
 };
@@ -266,24 +269,29 @@ cudaError_t launch_ragged(chessfad_ragged_plan_s *pl, const RaggedArgs &a, cudaS
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (pl->grid_dev != dev) {
-        if (pl->smem > 48 * 1024) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lk(pl->mu);
+        if (pl->grid_dev != dev) {
+            if (pl->smem > 48 * 1024) {
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem);
+                if (e != cudaSuccess) return e;
+            }
+            int per_sm = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRaggedBlock, pl->smem);
             if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            pl->grid = std::max(1, per_sm) * sms;
+            pl->grid_dev = dev;
         }
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRaggedBlock, pl->smem);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        pl->grid = std::max(1, per_sm) * sms;
-        pl->grid_dev = dev;
+        grid = pl->grid;
     }
     if (a.ntiles == 0) return cudaSuccess;
     // queue counter, per-request row counters and accumulators: contiguous
     e = cudaMemsetAsync(a.counter, 0, pl->total - pl->off_counter, stream);
     if (e != cudaSuccess) return e;
-    kern<<<std::min(pl->grid, a.ntiles), kRaggedBlock, pl->smem, stream>>>(a);
+    kern<<<std::min(grid, a.ntiles), kRaggedBlock, pl->smem, stream>>>(a);
     return cudaGetLastError();
 }
 

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <atomic>
+#include <mutex>
 #include <type_traits>
 
 #include "hdual.cuh"
@@ -943,20 +945,30 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
 }
 
 // Host-side launch helpers: compute the layout, opt into large dynamic
-// shared memory once per (kernel, device), launch, report the error.
+// shared memory once per (kernel, device), launch, report the error.  The
+// per-device record of the limit already set only grows, and it is read and
+// raised under one lock, so launches from several host threads never see the
+// limit lowered under them.
+inline std::mutex &smem_attr_mutex()
+{
+    static std::mutex mu;
+    return mu;
+}
+
 template <typename K>
-cudaError_t opt_in_smem(K kern, size_t bytes, int *configured)
+cudaError_t opt_in_smem(K kern, size_t bytes, std::atomic<int> *configured)
 {
     if (bytes <= 48 * 1024) return cudaSuccess;
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) dev = 0;
-    if (configured[dev] < (int)bytes) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        configured[dev] = (int)bytes;
-    }
-    return cudaSuccess;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (configured[dev].load(std::memory_order_acquire) >= (int)bytes) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(smem_attr_mutex());
+    if (configured[dev].load(std::memory_order_relaxed) >= (int)bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) configured[dev].store((int)bytes, std::memory_order_release);
+    return e;
 }
 
 template <typename T, typename IO, int C, int FN, bool HVP, int MB>
@@ -964,7 +976,7 @@ cudaError_t launch_sweep(SweepArgs a, int block_threads, cudaStream_t stream)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
     auto kern = sweep_kernel<T, IO, C, FN, HVP, MB>;
-    static int configured[64] = {0};
+    static std::atomic<int> configured[64];
     cudaError_t e = opt_in_smem(kern, L.total, configured);
     if (e != cudaSuccess) return e;
     const long long threads = a.batch * (long long)a.tpp;
@@ -987,7 +999,7 @@ cudaError_t launch_sym(SweepArgs a, cudaStream_t stream)
 {
     const size_t bytes = sym_smem_bytes<T, IO, C, FN, HVP, MB>(a);
     auto kern = sym_kernel<T, IO, C, FN, HVP, MB, kSparse>;
-    static int configured[64] = {0};
+    static std::atomic<int> configured[64];
     cudaError_t e = opt_in_smem(kern, bytes, configured);
     if (e != cudaSuccess) return e;
     const long long blocks = (a.batch + a.maxpts - 1) / a.maxpts;

@@ -109,6 +109,46 @@ def test_untuned_default_is_symmetric_at_the_sec5_chunk():
                 assert cf.chessfad_default_config(fn, n, 4096, prec).method == cf.PLAIN
 
 
+def test_default_threads_per_point_capped_by_items():
+    """The untuned symmetric default never gives a point more threads than it
+    has (row, chunk) items C nch (nch+1)/2 (rounded up to a power of two, at
+    least 8): at n = 4, c = 2 a point has 6 items, so 8 threads."""
+    for fn in (0, 1, 2):
+        for prec in (0, 1):
+            for n in (4, 5, 8, 12, 16, 64, 256):
+                for batch in (1, 100, 4096, 1 << 20):
+                    c = cf.chessfad_default_config(fn, n, batch, prec)
+                    nch = -(-n // c.csize)
+                    items = c.csize * nch * (nch + 1) // 2
+                    cap = max(8, 1 << (items - 1).bit_length())
+                    assert 8 <= c.threads_per_point <= min(256, cap), (fn, prec, n, batch, c.as_dict())
+    assert cf.chessfad_default_config(0, 4, 4096, 0).threads_per_point == 8
+
+
+def test_csize0_chunk_follows_the_method():
+    """csize 0 with an explicit method: the symmetric methods take the Sec. V
+    chunk sqrt(n/2), the one-thread-per-point method the plain method's
+    register-resident chunk; method 0 means the default method."""
+    import math
+
+    for fn in (0, 1, 2):
+        for prec in (0, 1):
+            d = cf.chessfad_default_config(fn, 64, 4096, prec)
+            assert cf.chessfad_resolve_config(fn, 64, 4096, prec, cf.Config(0, 0, 0, 0, 0)).as_dict() == d.as_dict()
+            assert cf.chessfad_resolve_config(fn, 64, 4096, prec).as_dict() == d.as_dict()
+            cap = 4 if (fn == 2 and prec == 0) else (8 if prec == 0 else 16)  # register budget
+            s = cf.chessfad_resolve_config(fn, 64, 4096, prec, cf.Config(0, 0, 0, cf.SYMMETRIC, 0))
+            assert s.method == cf.SYMMETRIC and s.csize == min(cap, 8) and 8 >= math.sqrt(32) > 4
+            p = cf.chessfad_resolve_config(fn, 64, 4096, prec, cf.Config(0, 0, 0, cf.POINT, 0))
+            assert p.method == cf.POINT and p.csize == cap
+            sp = cf.chessfad_resolve_config(fn, 64, 4096, prec, cf.Config(0, 0, 0, cf.SYMMETRIC_SPARSE, 0))
+            assert sp.method == cf.SYMMETRIC_SPARSE and sp.csize in (4, 8, 16)
+            # an explicit chunk size with method 0 is the plain method
+            assert cf.chessfad_resolve_config(fn, 64, 4096, prec, cf.Config(4, 1, 256, 0, 0)).method == cf.PLAIN
+    with pytest.raises(cf.ChessfadError):
+        cf.chessfad_resolve_config(0, 64, 4096, 0, cf.Config(3, 0, 0, 0, 0))
+
+
 @pytest.mark.parametrize("fn", [0, 1, 2])
 @pytest.mark.parametrize("prec", [0, 1])
 def test_default_config_host_only(fn, prec):
