@@ -9,7 +9,7 @@ The arithmetic lives in ``oracle.c`` (plain C, double precision, no fast-math,
 no FMA contraction).  Two independent implementations are exposed:
 
 * O1, closed forms: :func:`value`, :func:`gradient`, :func:`hessian`,
-  :func:`hvp`, :func:`hessian_batch`, :func:`hvp_ragged`.  Every chunked
+  :func:`hvp`, :func:`hessian_batch`, :func:`hvp_ragged`, :func:`fp_hvp`.  Every chunked
   method of the paper reaches the dense Hessian exactly up to rounding
   (Sec. III-B, Alg. 5), so H(x) and r = H(x) v by their plain definitions are
   the reference.
@@ -86,6 +86,8 @@ def _load():
             lib.orc_hvp_batch.argtypes = [I, I, L, P, P, P, P, P]
             lib.orc_hessian_batch.argtypes = [I, I, L, P, P, P]
             lib.orc_hvp_ragged.argtypes = [L, P, P, P, P, P, P, P, P, P, I, P, P]
+            lib.orc_fp_hvp.argtypes = [I, P, P, P, P, P]
+            lib.orc_fp_hvp.restype = I
             for name in ("orc_chunk_hess", "orc_schunk_hess"):
                 getattr(lib, name).argtypes = [I, I, I, P, P, P]
             for name in ("orc_chess_vec", "orc_sc_hess_vec"):
@@ -190,6 +192,20 @@ def hessian_batch(fn: int, x, params: FPParams | None = None) -> np.ndarray:
     if _load().orc_hessian_batch(fn, n, batch, _ptr(x), _params(fn, params), _ptr(H)) != 0:
         raise ValueError("oracle failure")
     return H
+
+
+def fp_hvp(x, v, params: FPParams):
+    """Fletcher-Powell r = H(x) v and ||H(x)||_F at one point, without forming
+    H: (H v)_j = 2 sum_m J_mj (J v)_m + 2 v_j (P^T r)_j, O(n^2) (the norm is
+    O(n^3))."""
+    x = _f64(x)
+    v = _f64(v)
+    out = np.empty_like(x)
+    hn = ctypes.c_double()
+    if _load().orc_fp_hvp(x.shape[-1], _ptr(x), _ptr(v), ctypes.byref(params._struct()), _ptr(out),
+                          ctypes.byref(hn)) != 0:
+        raise MemoryError
+    return out, hn.value
 
 
 def hvp_ragged(fns, ns, offs, eoffs, xpack, vpack, A=None, B=None, Epack=None, ld=0):

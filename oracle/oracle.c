@@ -225,6 +225,80 @@ static void fp_h(int n, const double *x, const orc_fp *p, double *H)
     free(r);
 }
 
+/* Fletcher-Powell Hessian-vector product without forming H, from the same
+ * closed form H = 2 J^T J + 2 diag(P^T r):
+ *   (H v)_j = 2 sum_m J_mj (sum_k J_mk v_k) + 2 v_j sum_m r_m P_mj,
+ * O(n^2) per point.  When hnorm is not NULL it also returns ||H||_F, from
+ * G = J^T J (accumulated row by row of J, upper triangle) and D_j =
+ * sum_m r_m P_mj:  ||H||_F^2 = 4 (sum_jk G_jk^2 + 2 sum_j G_jj D_j +
+ * sum_j D_j^2). */
+static int fp_hvp(int n, const double *x, const double *v, const orc_fp *p, double *out, double *hnorm)
+{
+    double *sn = (double *)malloc(sizeof(double) * n);
+    double *cs = (double *)malloc(sizeof(double) * n);
+    double *J = (double *)malloc(sizeof(double) * (size_t)n * n);
+    double *r = (double *)malloc(sizeof(double) * n);
+    double *Jv = (double *)malloc(sizeof(double) * n);
+    double *D = (double *)malloc(sizeof(double) * n);
+    if (!sn || !cs || !J || !r || !Jv || !D) {
+        free(sn); free(cs); free(J); free(r); free(Jv); free(D);
+        return -1;
+    }
+    for (int j = 0; j < n; ++j) {
+        sn[j] = sin(x[j]);
+        cs[j] = cos(x[j]);
+        D[j] = 0.0;
+        out[j] = 0.0;
+    }
+    for (int m = 0; m < n; ++m) {
+        const double *Am = p->A + (size_t)m * p->ld, *Bm = p->B + (size_t)m * p->ld;
+        double *Jm = J + (size_t)m * n;
+        double s = 0.0, jv = 0.0;
+        for (int j = 0; j < n; ++j) {
+            s += Am[j] * sn[j] + Bm[j] * cs[j];
+            Jm[j] = Am[j] * cs[j] - Bm[j] * sn[j];
+            jv += Jm[j] * v[j];
+        }
+        r[m] = p->E[m] - s;
+        Jv[m] = jv;
+    }
+    for (int m = 0; m < n; ++m) {
+        const double *Am = p->A + (size_t)m * p->ld, *Bm = p->B + (size_t)m * p->ld;
+        const double *Jm = J + (size_t)m * n;
+        for (int j = 0; j < n; ++j) {
+            out[j] += Jm[j] * Jv[m];
+            D[j] += r[m] * (Am[j] * sn[j] + Bm[j] * cs[j]);
+        }
+    }
+    for (int j = 0; j < n; ++j) out[j] = 2.0 * out[j] + 2.0 * D[j] * v[j];
+    int rc = 0;
+    if (hnorm) {
+        double *G = (double *)calloc((size_t)n * n, sizeof(double));
+        if (!G) {
+            rc = -1;
+        } else {
+            for (int m = 0; m < n; ++m) {
+                const double *Jm = J + (size_t)m * n;
+                for (int j = 0; j < n; ++j) {
+                    const double a = Jm[j];
+                    double *Gj = G + (size_t)j * n;
+                    for (int k = j; k < n; ++k) Gj[k] += a * Jm[k];
+                }
+            }
+            double off = 0.0, diag = 0.0;
+            for (int j = 0; j < n; ++j) {
+                const double *Gj = G + (size_t)j * n;
+                for (int k = j + 1; k < n; ++k) off += Gj[k] * Gj[k];
+                diag += Gj[j] * Gj[j] + 2.0 * Gj[j] * D[j] + D[j] * D[j];
+            }
+            *hnorm = 2.0 * sqrt(2.0 * off + diag);
+            free(G);
+        }
+    }
+    free(sn); free(cs); free(J); free(r); free(Jv); free(D);
+    return rc;
+}
+
 /* Test function of the extended operator set.  Sec. IV lists division, abs
  * and comparisons among the overloaded operators, but none of the paper's
  * three test functions uses them; this function does (it is defined here,
@@ -382,7 +456,8 @@ int orc_hessian_batch(int fn, int n, long long batch, const double *x, const orc
 
 /* Ragged reference HVPs: request q has function fn[q], size nv[q], and its
  * x, v, out start at off[q] in the packed arrays; Fletcher-Powell request q
- * uses E = Epack + eoff[q] with the shared A, B (leading dimension ld). */
+ * uses E = Epack + eoff[q] with the shared A, B (leading dimension ld) and is
+ * evaluated by fp_hvp (O(n^2) without forming H; O(n^3) for its norm). */
 int orc_hvp_ragged(long long nreq, const int *fn, const int *nv, const long long *off,
                    const long long *eoff, const double *xpack, const double *vpack,
                    const double *A, const double *B, const double *Epack, int ld,
@@ -393,6 +468,10 @@ int orc_hvp_ragged(long long nreq, const int *fn, const int *nv, const long long
     for (long long q = 0; q < nreq; ++q) {
         int n = nv[q];
         orc_fp p = { A, B, Epack ? Epack + (eoff ? eoff[q] : 0) : NULL, ld };
+        if (fn[q] == ORC_FLETCHER_POWELL) {
+            bad |= (fp_hvp(n, xpack + off[q], vpack + off[q], &p, outpack + off[q], hnorm ? hnorm + q : NULL) != 0);
+            continue;
+        }
         double *H = (double *)malloc(sizeof(double) * (size_t)n * n);
         if (!H) { bad |= 1; continue; }
         bad |= (orc_hessian(fn[q], n, xpack + off[q], &p, H) != 0);
@@ -423,6 +502,13 @@ int orc_hvp_ragged(long long nreq, const int *fn, const int *nv, const long long
  * Operation counters follow Sec. V: scalar multiplications and additions
  * (a subtraction counts as an addition). */
 static _Thread_local long long cnt_mul, cnt_add;
+
+/* Fletcher-Powell H v (and ||H||_F when hnorm is not NULL) without forming
+ * H; exported for the pins against H from fp_h times v. */
+int orc_fp_hvp(int n, const double *x, const double *v, const orc_fp *p, double *out, double *hnorm)
+{
+    return fp_hvp(n, x, v, p, out, hnorm);
+}
 
 void orc_count_reset(void) { cnt_mul = 0; cnt_add = 0; }
 void orc_count_get(long long *mul, long long *add) { *mul = cnt_mul; *add = cnt_add; }

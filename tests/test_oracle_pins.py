@@ -404,9 +404,39 @@ def test_ragged_equals_dense(orc):
             inst = rg.fp.leading(n)
             p = orc.FPParams(inst.A, inst.B, inst.E)
             np.testing.assert_allclose(rg.Epack[rg.eoffs[q]:rg.eoffs[q] + n], inst.E, rtol=1e-15, atol=1e-12)
-        r, h = orc.hvp(fn, rg.xpack[o:o + n][None], rg.vpack[o:o + n][None], p, with_norm=True)
-        np.testing.assert_allclose(out[o:o + n], r[0], rtol=1e-13, atol=1e-9)
+        v = rg.vpack[o:o + n]
+        r, h = orc.hvp(fn, rg.xpack[o:o + n][None], v[None], p, with_norm=True)
+        if fn == F:
+            # evaluated without forming H (fp_hvp): the same values up to the
+            # summation order
+            assert np.linalg.norm(out[o:o + n] - r[0]) <= 1e-14 * h[0] * np.linalg.norm(v)
+        else:
+            np.testing.assert_allclose(out[o:o + n], r[0], rtol=1e-13, atol=1e-9)
         assert abs(hn[q] - h[0]) <= 1e-13 * h[0]
+
+
+def test_fp_hvp_without_forming_h(orc):
+    """(H v)_j = 2 sum_m J_mj (J v)_m + 2 v_j (P^T r)_j equals the closed-form
+    Hessian times v, and its norm the Frobenius norm of that Hessian; at
+    n = 1 with A = 1, B = 0, E = 0 (f = sin^2 x) it is 2 cos(2x) v."""
+    x = np.array([0.37])
+    p = orc.FPParams([[1.0]], [[0.0]], [0.0])
+    r, h = orc.fp_hvp(x, np.array([0.5]), p)
+    assert abs(r[0] - math.cos(0.74)) < 1e-15 and abs(h - 2 * abs(math.cos(0.74))) < 1e-15
+    p = orc.FPParams([[0.0]], [[1.0]], [1.0])  # f = (1 - cos x)^2
+    r, h = orc.fp_hvp(x, np.array([-2.0]), p)
+    assert abs(r[0] + 2 * (2 * math.cos(0.37) - 2 * math.cos(0.74))) < 1e-14
+    for n in (2, 3, 5, 33, 100):
+        inst = _fp(n, seed=40 + n)
+        p = orc.FPParams(inst.A, inst.B, inst.E)
+        rng = np.random.Generator(np.random.PCG64(n))
+        for k in range(3):
+            x = rng.uniform(-math.pi, math.pi, n) if k else inst.alpha  # at the solution r = 0
+            v = rng.uniform(-1, 1, n)
+            H = orc.hessian(F, x, p)
+            r, h = orc.fp_hvp(x, v, p)
+            assert np.linalg.norm(r - H @ v) <= 1e-14 * np.linalg.norm(H) * np.linalg.norm(v), (n, k)
+            assert abs(h - np.linalg.norm(H)) <= 1e-13 * np.linalg.norm(H), (n, k)
 
 
 # ------------------------------------------------------------------ Sec. V counts
