@@ -282,20 +282,50 @@ typedef struct chessfad_ragged_plan_s *chessfad_ragged_plan;
 
 /* Build a plan (host memory, owned by the caller until
  * chessfad_ragged_plan_destroy) from a host array of nreq requests for
- * precision prec with chunk size csize (8 or 16; 0 = 16 for compensated FP32,
- * 8 for FP64).  Validates every request: CHESSFAD_ERR_FUNCTION / _SIZE for a
- * bad fn or n,
+ * precision prec.  csize 8 or 16: every (function, n) group uses that chunk
+ * size and the default lanes per row; csize 0: each group takes the chunk
+ * size and lanes per row that chessfad_ragged_autotune stored for its
+ * (precision, function, n range), else the defaults (chunk 16 for compensated
+ * FP32, 8 for FP64; lanes per row min(32, pow2_floor(ceil(n/C) / 8))).  The
+ * n ranges are the powers of two, 2^b <= n < 2^(b+1) (n = 512 with 256..511).
+ * Validates every request: CHESSFAD_ERR_FUNCTION / _SIZE for a bad fn or n,
  * CHESSFAD_ERR_PLAN for a negative offset.  Launches nothing. */
 CHESSFAD_API int chessfad_ragged_plan_create(const chessfad_request *reqs, long long nreq, int prec, int csize,
                                              chessfad_ragged_plan *plan);
 CHESSFAD_API int chessfad_ragged_plan_destroy(chessfad_ragged_plan plan);
 
 /* Device workspace bytes the plan needs (tile table, request list, offsets,
- * the queue counter, and for the Fletcher-Powell requests with n >= 128 a row
- * counter and n FP64 accumulators each), the number of tiles and the dynamic
- * shared memory per CTA.  Any pointer may be NULL. */
+ * the queue counter, a tile counter per request and, for the Fletcher-Powell
+ * requests with n >= 128, one FP64 partial row vector per tile), the number
+ * of tiles and the dynamic shared memory per CTA.  Any pointer may be NULL. */
 CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes, long long *ntiles,
                                            size_t *smem_bytes);
+
+/* The chunk size and lanes per row the plan uses for requests of function fn
+ * and size n (CHESSFAD_ERR_SIZE if it holds no such request).  Host only. */
+CHESSFAD_API int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, int fn, int n, int *csize,
+                                                   int *threads_per_row);
+
+/* Autotune the uneven batch: for every (function, n range) group of the
+ * requests (ranges as for chessfad_ragged_plan_create), time the persistent
+ * kernel on a sample of the group's requests (in table order, enough rows to
+ * fill the GPU about four times) for every chunk size (16, 8) and lanes per
+ * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values), and
+ * store the fastest per (prec, function, n range) in the process-wide table
+ * that chessfad_ragged_plan_create(..., csize = 0, ...) reads.  xpack, vpack,
+ * outpack, params as for chessfad_hvp_ragged (outpack of the sampled requests
+ * is overwritten); workspace: device scratch of workspace_bytes (candidates
+ * whose trial plan needs more are skipped; the workspace of a plan of all
+ * the requests is enough).  *groups_tuned (may be NULL) receives the number
+ * of groups stored.  Synchronises `stream`; allocates no device memory. */
+CHESSFAD_API int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int prec, const void *xpack,
+                                          const void *vpack, void *outpack, const chessfad_fp_params *params,
+                                          void *workspace, size_t workspace_bytes, chessfad_stream_t stream,
+                                          long long *groups_tuned);
+
+/* The tuned (chunk size, lanes per row) of (prec, fn, n's range), or
+ * CHESSFAD_ERR_CONFIG if that group has not been tuned.  Host only. */
+CHESSFAD_API int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threads_per_row);
 
 /* Copy the plan's tables into a caller-allocated device workspace of at least
  * workspace_bytes (cudaMemcpyAsync on stream from the plan's host memory;
@@ -303,16 +333,16 @@ CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *wo
 CHESSFAD_API int chessfad_ragged_plan_upload(chessfad_ragged_plan plan, void *workspace, size_t workspace_bytes,
                                              chessfad_stream_t stream);
 
-/* Run the plan: reset the queue counter, row counters and accumulators in the
- * workspace (one cudaMemsetAsync) and launch one persistent kernel, both on
- * stream; no host synchronisation, no allocation, so the call can be captured
- * into a CUDA graph and replayed.  Fletcher-Powell requests with n >= 128 use
- * the symmetric method (SC-HESS-VEC, Alg. 8; about half the evaluations):
- * each entry right of a row's diagonal chunk also updates the row it mirrors,
- * usually in another tile, through FP64 atomic adds, and the tile finishing a
- * request's last rows rounds its accumulators into outpack.  The FP64
- * addition order varies, so FP64 results of those requests can differ from
- * run to run in the last bits; everything else is bitwise reproducible.
+/* Run the plan: reset the queue counter and the per-request tile counters in
+ * the workspace (one cudaMemsetAsync) and launch one persistent kernel, both
+ * on stream; no host synchronisation, no allocation, so the call can be
+ * captured into a CUDA graph and replayed.  Fletcher-Powell requests with
+ * n >= 128 use the symmetric method (SC-HESS-VEC, Alg. 8; about half the
+ * evaluations): each entry right of a row's diagonal chunk also updates the
+ * row it mirrors, usually in another tile; every tile adds its rows'
+ * contributions in a fixed order into a partial row vector of its own (FP64)
+ * and the tile that completes a request adds the request's partial vectors
+ * in tile order, so every result is bitwise reproducible from run to run.
  * xpack, vpack, outpack: device, float (FP32_COMP) or double (FP64) by the
  * plan's precision.  params: required when the plan holds Fletcher-Powell
  * requests (ld >= their largest n).  Runs that share a workspace must not
@@ -327,11 +357,11 @@ CHESSFAD_API int chessfad_hvp_ragged(chessfad_ragged_plan plan, const void *xpac
  * device, or real-time code with no room for allocation latency.  The paper
  * has no counterpart; it is a deployment convenience.
  *
- * The scratch (the plan's tables, counters and accumulators) lives in a
+ * The scratch (the plan's tables, counters and partial row vectors) lives in a
  * static device array of CHESSFAD_RAGGED_STATIC_BYTES that every GPU which
  * loads the library holds until the process exits.  Each call copies the
  * plan's tables into it from the plan's host memory (cudaMemcpyAsync on
- * stream), zeroes the counters and accumulators (cudaMemsetAsync) and
+ * stream), zeroes the counters (cudaMemsetAsync) and
  * launches the persistent kernel; it allocates nothing and calls no
  * allocating routine.  Keep the plan alive for as long as any work issued by
  * a call with it may still run.
@@ -382,7 +412,9 @@ CHESSFAD_API int chessfad_version(void);
  * stands).  params is the caller's device pointer, passed through (may be
  * NULL).  The arithmetic of f runs in the handle's precision: FP64, or FP32
  * (CHESSFAD_FP32_COMP: only the row-times-v reduction is compensated; the
- * function's own sums are plain FP32 as written).
+ * function's own sums are plain FP32 as written; at n = 1, where the Hessian
+ * is one entry whose terms can cancel, the arithmetic is FP64 with float
+ * inputs and outputs).
  *
  * Two decompositions, as for the built-in functions: plain (CHESS-VEC,
  * Alg. 7 / CHUNK-HESS, Alg. 5: one thread per (point, Hessian row), sweeping

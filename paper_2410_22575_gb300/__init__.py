@@ -91,6 +91,9 @@ def load(build_if_missing: bool = True):
         lib.chessfad_ragged_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(L),
                                                   ctypes.POINTER(ctypes.c_size_t)]
         lib.chessfad_ragged_plan_upload.argtypes = [P, P, ctypes.c_size_t, P]
+        lib.chessfad_ragged_plan_group_config.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.chessfad_ragged_autotune.argtypes = [P, L, I, P, P, P, P, P, ctypes.c_size_t, P, ctypes.POINTER(L)]
+        lib.chessfad_ragged_tuned_config.argtypes = [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.chessfad_hvp_ragged.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
         lib.chessfad_hvp_ragged_noalloc.argtypes = [P, P, P, P, P, P]
         lib.chessfad_hvp_ragged_noalloc.restype = I
@@ -118,7 +121,8 @@ def load(build_if_missing: bool = True):
                      "chessfad_peak_info",
                      "chessfad_kernel_info", "chessfad_version", "chessfad_ragged_plan_create",
                      "chessfad_ragged_plan_destroy", "chessfad_ragged_plan_info", "chessfad_ragged_plan_upload",
-                     "chessfad_hvp_ragged"):
+                     "chessfad_hvp_ragged", "chessfad_ragged_plan_group_config", "chessfad_ragged_autotune",
+                     "chessfad_ragged_tuned_config"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -345,6 +349,32 @@ def chessfad_hvp_ragged(plan, xpack, vpack, outpack, params, workspace, workspac
     p = ctypes.byref(params) if params is not None else None
     return load().chessfad_hvp_ragged(plan, _addr(xpack), _addr(vpack), _addr(outpack), p, _addr(workspace),
                                       workspace_bytes, _stream(stream))
+
+
+def chessfad_ragged_plan_group_config(plan, fn, n) -> tuple[int, int]:
+    c, t = ctypes.c_int(), ctypes.c_int()
+    _check(load().chessfad_ragged_plan_group_config(plan, fn, n, ctypes.byref(c), ctypes.byref(t)),
+           "chessfad_ragged_plan_group_config")
+    return c.value, t.value
+
+
+def chessfad_ragged_autotune(reqs, prec, xpack, vpack, outpack, params, workspace, workspace_bytes,
+                             stream=None) -> int:
+    """Tune (chunk size, lanes per row) per (function, n range) of the
+    requests; returns the number of groups stored."""
+    g = ctypes.c_longlong()
+    p = ctypes.byref(params) if params is not None else None
+    _check(load().chessfad_ragged_autotune(reqs.ctypes.data if len(reqs) else None, len(reqs), prec, _addr(xpack),
+                                           _addr(vpack), _addr(outpack), p, _addr(workspace), workspace_bytes,
+                                           _stream(stream), ctypes.byref(g)), "chessfad_ragged_autotune")
+    return g.value
+
+
+def chessfad_ragged_tuned_config(prec, fn, n):
+    """(csize, threads_per_row) tuned for (prec, fn, n's range), or None."""
+    c, t = ctypes.c_int(), ctypes.c_int()
+    st = load().chessfad_ragged_tuned_config(prec, fn, n, ctypes.byref(c), ctypes.byref(t))
+    return None if st != SUCCESS else (c.value, t.value)
 
 
 def chessfad_hvp_ragged_noalloc(plan, xpack, vpack, outpack, params=None, stream=None) -> int:

@@ -853,11 +853,15 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
     const PointTables<T> pt(smem_raw, L, active ? q : 0, n);
     T *Hs = reinterpret_cast<T *>(smem_raw + align_up(L.total, 16) + (size_t)(active ? q : 0) * sym_hs_bytes<T>(n, C));
     // Accumulator form of the HVP (points whose chunk matrix does not fit
-    // shared memory): one FP64 accumulator per row of each staged point.
-    double *accs = reinterpret_cast<double *>(smem_raw + align_up(L.total, 16)) + (size_t)(active ? q : 0) * n;
+    // shared memory): one FP64 accumulator per row of each staged point, and
+    // a per-iteration stage of every thread's chunk (see below).
+    double *accs_all = reinterpret_cast<double *>(smem_raw + align_up(L.total, 16));
+    double *accs = accs_all + (size_t)(active ? q : 0) * n;
     const bool acc_form = HVP && a.sym_acc;
+    SymStage<T, C> stage(smem_raw + align_up(L.total, 16) + align_up((size_t)ppb * n * sizeof(double), 16),
+                         (int)blockDim.x);
     if (acc_form) {
-        for (int e = tid; e < npts * n; e += blockDim.x) reinterpret_cast<double *>(smem_raw + align_up(L.total, 16))[e] = 0.0;
+        for (int e = tid; e < npts * n; e += blockDim.x) accs_all[e] = 0.0;
         __syncthreads();
     }
 
@@ -872,34 +876,51 @@ __global__ void __launch_bounds__(256, 1) sym_kernel(const SweepArgs a)
             sym_item(k, C, nch, i, cn);
             has = i < n;
         }
-        if (FN != FN_FP && !has) continue;
+        if (FN != FN_FP && !has && !acc_form) continue;
         const int cstart = cn * C;
         const HD<T, C> f = row_chunk<T, C, FN, MB, true, kSparse>(job, smem_raw, L, pt, i, cstart, has, it == 0);
-        if (!has) continue;
         if constexpr (HVP) {
             if (acc_form) {
-                // r_i += sum_l H_il v_l; off the diagonal chunk also r_l += H_il v_i
-                // (Alg. 8's two updates), into FP64 (products of two FP32 values
-                // are exact there)
-                const bool mirror = cn > i / C;
-                const double vi = (double)pt.v[i];
+                // Alg. 8's two updates, r_i += sum_l H_il v_l and, off the
+                // diagonal chunk, r_l += H_il v_i, made reproducible: every
+                // thread stages its chunk and its row dot (FP64; products of
+                // two FP32 values are exact there), then each thread adds, for
+                // the rows it owns, the staged contributions of its point's
+                // threads in thread order.
                 double own = 0.0;
+                if (has) {
 #pragma unroll
-                for (int l = 0; l < C; ++l) {
-                    const int j = cstart + l;
-                    if (j < n) {
-                        own = fma((double)f.h[l], (double)pt.v[j], own);
-                        if (mirror) atomicAdd(&accs[j], (double)f.h[l] * vi);
+                    for (int l = 0; l < C; ++l)
+                        if (cstart + l < n) own = fma((double)f.h[l], (double)pt.v[cstart + l], own);
+                }
+                stage.put(tid, f.h, own, has ? i : -1, cn);
+                __syncthreads();
+                if (active) {
+                    const int t0 = q * tpp;
+                    for (int srow = t; srow < n; srow += tpp) {
+                        const int scn = srow / C, sl = srow - scn * C;
+                        double acc = accs[srow];
+                        for (int u = 0; u < tpp; ++u) {
+                            const int ui = stage.row(t0 + u);
+                            if (ui < 0) continue;
+                            if (ui == srow) acc += stage.own(t0 + u);
+                            const int ucn = stage.chunk(t0 + u);
+                            if (ucn == scn && ucn > ui / C)
+                                acc += (double)stage.h(t0 + u, sl) * (double)pt.v[ui];
+                        }
+                        accs[srow] = acc;
                     }
                 }
-                atomicAdd(&accs[i], own);
-            } else {
-                T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
-#pragma unroll
-                for (int l = 0; l < C; ++l)
-                    if (cstart + l < n) hrow[cstart + l] = f.h[l];
+                __syncthreads();
+                continue;
             }
+            if (!has) continue;
+            T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
+#pragma unroll
+            for (int l = 0; l < C; ++l)
+                if (cstart + l < n) hrow[cstart + l] = f.h[l];
         } else {
+            if (!has) continue;
             IO *H = reinterpret_cast<IO *>(a.out) + (size_t)p * n * n;
             const bool mirror = cn > i / C;
 #pragma unroll
@@ -990,7 +1011,9 @@ template <typename T, typename IO, int C, int FN, bool HVP, int MB>
 size_t sym_smem_bytes(const SweepArgs &a)
 {
     const Smem<T> L = smem_layout<T>(FN, HVP, a.n, a.maxpts, a.mt);
-    if (HVP && a.sym_acc) return align_up(L.total, 16) + (size_t)a.maxpts * a.n * sizeof(double);
+    if (HVP && a.sym_acc)
+        return align_up(L.total, 16) + align_up((size_t)a.maxpts * a.n * sizeof(double), 16) +
+               (size_t)SymStage<T, C>::bytes(a.maxpts * a.tpp);
     return align_up(L.total, 16) + (HVP ? (size_t)a.maxpts * sym_hs_bytes<T>(a.n, C) : 0);
 }
 

@@ -29,6 +29,8 @@ struct chessfad_user_fn {
     cudaKernel_t hessian = nullptr;      // plain (CHUNK-HESS, Alg. 5)
     cudaKernel_t sym_hvp = nullptr;      // symmetric (SC-HESS-VEC, Alg. 8)
     cudaKernel_t sym_hessian = nullptr;  // symmetric (SCHUNK-HESS, Alg. 6)
+    cudaKernel_t hvp_n1 = nullptr;       // FP32 handles, n = 1: FP64 arithmetic, float I/O
+    cudaKernel_t hessian_n1 = nullptr;
     int csize = 0;
     int prec = 0;
     std::mutex mu;
@@ -155,8 +157,12 @@ int resolve(const chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, in
         if (tpp > bt) bt = tpp;
         // staged chunk matrix, else (HVP) FP64 row accumulators
         for (int form = 0; form < (hvp ? 2 : 1); ++form) {
+            // form 1 (accumulators): per point n FP64 accumulators, x, v and
+            // the per-iteration stage of its threads (C values, an FP64 row
+            // dot and two ints each), plus 32 bytes of alignment
             const size_t per_pt = form == 0 ? ((size_t)n * (hvp ? 2 : 1) + (hvp ? (size_t)hs_elems(n, fn->csize) : 0)) * elem
-                                            : (size_t)n * 2 * elem + (size_t)n * sizeof(double);
+                                            : (size_t)n * 2 * elem + (size_t)n * sizeof(double) +
+                                                  (size_t)tpp * ((size_t)fn->csize * elem + sizeof(double) + 2 * sizeof(int)) + 32;
             long long p = bt / tpp;
             if (p > batch) p = batch;
             while (p > 1 && (size_t)p * per_pt > kSmemBudget) --p;
@@ -193,7 +199,20 @@ int launch(chessfad_user_fn *fn, const chessfad_config *cfg, bool hvp, int n, lo
     long long grid;
     unsigned block;
     cudaKernel_t k;
-    if (method == CHESSFAD_METHOD_SYMMETRIC) {
+    if (fn->prec == CHESSFAD_FP32_COMP && n == 1) {
+        // one variable: the FP64 kernel with float I/O (a single Hessian
+        // entry whose terms can cancel), by the plain decomposition (the
+        // symmetric one has the same single item)
+        const int b = bt > 0 ? bt : kBlock;
+        const long long per_cta = b + 1;
+        args.maxpts = (int)(batch < per_cta ? batch : per_cta);
+        args.tpp = 1;
+        args.acc = 0;
+        grid = (batch + b - 1) / b;
+        block = (unsigned)b;
+        smem = (size_t)args.maxpts * 2 * sizeof(double);
+        k = hvp ? fn->hvp_n1 : fn->hessian_n1;
+    } else if (method == CHESSFAD_METHOD_SYMMETRIC) {
         grid = (batch + ppb - 1) / ppb;
         block = (unsigned)(ppb * tpp);
         k = hvp ? fn->sym_hvp : fn->sym_hessian;
@@ -257,8 +276,9 @@ CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, i
     const std::string def_t = std::string("-DCHESSFAD_USER_T=") + (prec == CHESSFAD_FP64 ? "double" : "float");
     const std::string def_c = "-DCHESSFAD_USER_C=" + std::to_string(csize);
     const std::string def_fn = std::string("-DCHESSFAD_USER_FN=") + name;
+    const std::string def_f32 = std::string("-DCHESSFAD_USER_F32=") + (prec == CHESSFAD_FP64 ? "0" : "1");
     const char *opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-default-device",
-                          def_t.c_str(), def_c.c_str(), def_fn.c_str()};
+                          def_t.c_str(), def_c.c_str(), def_fn.c_str(), def_f32.c_str()};
     const nvrtcResult cr = rt.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
     size_t lsz = 0;
     rt.log_size(prog, &lsz);
@@ -289,6 +309,9 @@ CHESSFAD_API int chessfad_user_fn_create(const char *source, const char *name, i
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->hessian, fn->lib, "chessfad_user_hessian");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->sym_hvp, fn->lib, "chessfad_user_sym_hvp");
     if (e == cudaSuccess) e = cudaLibraryGetKernel(&fn->sym_hessian, fn->lib, "chessfad_user_sym_hessian");
+    if (e == cudaSuccess && prec == CHESSFAD_FP32_COMP) e = cudaLibraryGetKernel(&fn->hvp_n1, fn->lib, "chessfad_user_hvp_n1");
+    if (e == cudaSuccess && prec == CHESSFAD_FP32_COMP)
+        e = cudaLibraryGetKernel(&fn->hessian_n1, fn->lib, "chessfad_user_hessian_n1");
     if (e != cudaSuccess) {
         cudaGetLastError();
         put_log(log, log_bytes, std::string("compiled; loading failed: ") + cudaGetErrorString(e));

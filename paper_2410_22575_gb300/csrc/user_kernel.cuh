@@ -18,7 +18,8 @@
 //    sums whole rows, each off-diagonal-chunk entry serving both r_i and r_j.
 // FP32: the row-times-v products are summed as a Dot2 (TwoProd by FMA plus
 // TwoSum); the function's own arithmetic is plain FP32, as written by the
-// user.  FP64: fused multiply-add accumulation.
+// user, except at n = 1 (FP64 arithmetic, float I/O).  FP64: fused
+// multiply-add accumulation.
 #pragma once
 
 #include "sym_layout.cuh"
@@ -55,7 +56,10 @@ struct RowDot<float> {
     __device__ __forceinline__ float value() const { return csum_value(s); }
 };
 
-template <typename T, int C, bool HVP>
+// T: the arithmetic type; IO: the element type of x, v and the output (IO =
+// T except for the one-variable kernels of an FP32 handle, which compute in
+// FP64 with float inputs and outputs).
+template <typename T, typename IO, int C, bool HVP>
 __device__ __forceinline__ void user_sweep(const UserArgs &a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -67,11 +71,11 @@ __device__ __forceinline__ void user_sweep(const UserArgs &a)
     const long long last = (first + blockDim.x <= items ? first + blockDim.x : items) - 1;
     const long long p0 = first / n;
     const int staged = (int)(last / n - p0 + 1) * n;
-    const T *xg = static_cast<const T *>(a.x) + p0 * n;
-    const T *vg = static_cast<const T *>(a.v) + p0 * n;
+    const IO *xg = static_cast<const IO *>(a.x) + p0 * n;
+    const IO *vg = static_cast<const IO *>(a.v) + p0 * n;
     for (int t = threadIdx.x; t < staged; t += blockDim.x) {
-        xs[t] = xg[t];
-        if (HVP) vs[t] = vg[t];
+        xs[t] = (T)xg[t];
+        if (HVP) vs[t] = (T)vg[t];
     }
     __syncthreads();
     const long long item = first + threadIdx.x;
@@ -92,13 +96,13 @@ __device__ __forceinline__ void user_sweep(const UserArgs &a)
             for (int l = 0; l < C; ++l)
                 if (cstart + l < n) dot.add(r.a.h[l], vp[cstart + l]);
         } else {
-            T *H = static_cast<T *>(a.out) + (p * n + i) * (long long)n + cstart;
+            IO *H = static_cast<IO *>(a.out) + (p * n + i) * (long long)n + cstart;
 #pragma unroll
             for (int l = 0; l < C; ++l)
-                if (cstart + l < n) H[l] = r.a.h[l];
+                if (cstart + l < n) H[l] = (IO)r.a.h[l];
         }
     }
-    if (HVP) static_cast<T *>(a.out)[p * n + i] = dot.value();
+    if (HVP) static_cast<IO *>(a.out)[p * n + i] = (IO)dot.value();
 }
 
 template <typename T, int C, bool HVP>
@@ -107,6 +111,7 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n, ppb = a.maxpts, tpp = a.tpp;
     // accumulators first (8-byte aligned), then x, v and the staged chunks
+    // (accumulator form: the per-iteration stage, SymStage, in their place)
     double *accs = reinterpret_cast<double *>(smem_raw);
     const bool acc_form = HVP && a.acc;
     T *xs = reinterpret_cast<T *>(smem_raw + (acc_form ? (size_t)ppb * n * sizeof(double) : 0));
@@ -131,29 +136,66 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
     const T z = opaque_zero<T>();
     const int nch = (n + C - 1) / C;
     const int items = C * nch * (nch + 1) / 2;
-    for (int k = active ? t : items; k < items; k += tpp) {
+    if (HVP && acc_form) {
+        // Alg. 8's two updates (r_i += sum_l H_il v_l; off the diagonal chunk
+        // also r_l += H_il v_i) in FP64, reproducibly: each iteration stages
+        // every thread's chunk and row dot (SymStage), and each thread adds
+        // the contributions to its own rows in thread order.  Every thread
+        // runs the same number of iterations (the barriers).
+        const size_t soff = ((size_t)(reinterpret_cast<unsigned char *>(hs) - smem_raw) + 15) / 16 * 16;
+        const SymStage<T, C> stage(smem_raw + soff, (int)blockDim.x);
+        const T *vp = vs + (size_t)q * n;
+        const int iters = (items + tpp - 1) / tpp;
+        for (int it = 0; it < iters; ++it) {
+            const int k = t + it * tpp;
+            int i = -1, cn = 0;
+            T h[C];
+            double own = 0.0;
+            if (active && k < items) {
+                sym_item(k, C, nch, i, cn);
+                if (i >= n) i = -1;
+            }
+            if (i >= 0) {
+                const int cstart = cn * C;
+                const Vars<T, C> x{xp, i, cstart, z};
+                const Num<T, C> r = ::CHESSFAD_USER_FN<Num<T, C>, Vars<T, C>>(x, n, a.params);
+#pragma unroll
+                for (int l = 0; l < C; ++l) {
+                    h[l] = r.a.h[l];
+                    if (cstart + l < n) own = fma((double)h[l], (double)vp[cstart + l], own);
+                }
+            } else {
+#pragma unroll
+                for (int l = 0; l < C; ++l) h[l] = T(0);
+            }
+            stage.put(threadIdx.x, h, own, i, cn);
+            __syncthreads();
+            if (active) {
+                const int t0 = q * tpp;
+                for (int srow = t; srow < n; srow += tpp) {
+                    const int scn = srow / C, sl = srow - scn * C;
+                    double sum = acc[srow];
+                    for (int u = 0; u < tpp; ++u) {
+                        const int ui = stage.row(t0 + u);
+                        if (ui < 0) continue;
+                        if (ui == srow) sum += stage.own(t0 + u);
+                        const int ucn = stage.chunk(t0 + u);
+                        if (ucn == scn && ucn > ui / C) sum += (double)stage.h(t0 + u, sl) * (double)vp[ui];
+                    }
+                    acc[srow] = sum;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int k = (active && !(HVP && acc_form)) ? t : items; k < items; k += tpp) {
         int i = 0, cn = 0;
         sym_item(k, C, nch, i, cn);
         if (i >= n) continue;
         const int cstart = cn * C;
         const Vars<T, C> x{xp, i, cstart, z};
         const Num<T, C> r = ::CHESSFAD_USER_FN<Num<T, C>, Vars<T, C>>(x, n, a.params);
-        if (HVP && acc_form) {
-            // r_i += sum_l H_il v_l; off the diagonal chunk also r_l += H_il v_i
-            const T *vp = vs + (size_t)q * n;
-            const bool mirror = cn > i / C;
-            const double vi = (double)vp[i];
-            double own = 0.0;
-#pragma unroll
-            for (int l = 0; l < C; ++l) {
-                const int j = cstart + l;
-                if (j < n) {
-                    own = fma((double)r.a.h[l], (double)vp[j], own);
-                    if (mirror) atomicAdd(&acc[j], (double)r.a.h[l] * vi);
-                }
-            }
-            atomicAdd(&acc[i], own);
-        } else if (HVP) {
+        if (HVP) {
             T *hrow = Hs + sym_hs_row(i, n, C) - (i / C) * C;
 #pragma unroll
             for (int l = 0; l < C; ++l)
@@ -208,10 +250,25 @@ extern "C" __global__ void __launch_bounds__(256) chessfad_user_sym_hessian(ches
 
 extern "C" __global__ void __launch_bounds__(256) chessfad_user_hvp(chessfad::user::UserArgs a)
 {
-    chessfad::user::user_sweep<CHESSFAD_USER_T, CHESSFAD_USER_C, true>(a);
+    chessfad::user::user_sweep<CHESSFAD_USER_T, CHESSFAD_USER_T, CHESSFAD_USER_C, true>(a);
 }
 
 extern "C" __global__ void __launch_bounds__(256) chessfad_user_hessian(chessfad::user::UserArgs a)
 {
-    chessfad::user::user_sweep<CHESSFAD_USER_T, CHESSFAD_USER_C, false>(a);
+    chessfad::user::user_sweep<CHESSFAD_USER_T, CHESSFAD_USER_T, CHESSFAD_USER_C, false>(a);
 }
+
+#if CHESSFAD_USER_F32
+// One variable in an FP32 handle: the Hessian is a single entry, a sum of
+// terms that can cancel far below their size, so no FP32 evaluation bounds
+// its relative error; it is computed in FP64 with float x, v and output.
+extern "C" __global__ void __launch_bounds__(256) chessfad_user_hvp_n1(chessfad::user::UserArgs a)
+{
+    chessfad::user::user_sweep<double, float, 1, true>(a);
+}
+
+extern "C" __global__ void __launch_bounds__(256) chessfad_user_hessian_n1(chessfad::user::UserArgs a)
+{
+    chessfad::user::user_sweep<double, float, 1, false>(a);
+}
+#endif

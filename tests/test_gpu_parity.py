@@ -190,8 +190,13 @@ def test_symmetric_hvp_accumulator_form(fn, prec):
             batch = 2
         d = Dev(W.make_batch(fn, n, batch, seed=60 + n), prec)
         for c, tpp in ((8, 64), (16, 128)):
-            e = hvp_err(d, d.hvp(cfg=cf.Config(c, 0, 0, cf.SYMMETRIC, tpp)))
+            cfg = cf.Config(c, 0, 0, cf.SYMMETRIC, tpp)
+            first = d.hvp(cfg=cfg)
+            e = hvp_err(d, first)
             assert e.max() <= BOUND[prec], (n, c, e.max())
+            # the accumulators add the staged contributions in thread order:
+            # bitwise reproducible
+            assert np.array_equal(first, d.hvp(cfg=cfg)), (n, c)
         e = hvp_err(d, d.hvp(cfg=cf.Config(8, 0, 0, cf.SYMMETRIC_SPARSE, 64)))
         assert e.max() <= BOUND[prec], (n, "sparse", e.max())
 

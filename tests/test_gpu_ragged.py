@@ -146,10 +146,12 @@ def _ragged_from(fns, ns, seed, nmax=320):
 @pytest.mark.parametrize("prec", [cf.FP64, cf.FP32_COMP])
 @pytest.mark.parametrize("csize", [8, 16])
 def test_symmetric_fletcher_powell_requests(prec, csize):
-    """Fletcher-Powell requests with n >= 128 run SC-HESS-VEC (Alg. 8) with
-    FP64 accumulators shared across tiles: sizes on and off tile and chunk
-    boundaries, two requests of one size, mixed with small requests of every
-    function; every request against the oracle, on two runs."""
+    """Fletcher-Powell requests with n >= 128 run SC-HESS-VEC (Alg. 8), each
+    tile adding its rows' contributions into a partial row vector and the
+    last tile of a request summing them in tile order: sizes on and off tile
+    and chunk boundaries, two requests of one size, mixed with small requests
+    of every function; every request against the oracle, and a second run
+    bit for bit equal to the first."""
     F, R, A = W.FLETCHER_POWELL, W.ROSENBROCK, W.ACKLEY
     fns = [F, R, F, A, F, F, R, F, A, F]
     ns = [128, 7, 131, 30, 200, 256, 300, 256, 150, 320]
@@ -158,9 +160,37 @@ def test_symmetric_fletcher_powell_requests(prec, csize):
     first = d.run()
     e = d.errors(first)
     assert e.max() <= BOUND[prec], (e.max(), np.median(e))
-    # the FP64 accumulation order varies between runs (atomic adds): the
-    # second run meets the same bound, not necessarily bit for bit
     d.out.fill_(float("nan"))
     second = d.run()
-    e2 = d.errors(second)
-    assert e2.max() <= BOUND[prec], (e2.max(), np.median(e2))
+    assert np.array_equal(first, second)
+
+
+def test_ragged_autotune_then_plan_parity():
+    """chessfad_ragged_autotune stores a (chunk size, lanes per row) per
+    (function, n range); a plan built with csize 0 uses them, and its results
+    meet the bounds against the oracle (every request)."""
+    import torch
+
+    F, R, A = W.FLETCHER_POWELL, W.ROSENBROCK, W.ACKLEY
+    rg = W.make_ragged(nreq=900, seed=31, nmax=200)
+    for prec in (cf.FP32_COMP, cf.FP64):
+        d = DevRagged(rg, prec, 16)
+        reqs = cf.requests(rg.fns, rg.ns, rg.offs, rg.eoffs)
+        ws = d.plan.workspace
+        tuned = cf.chessfad_ragged_autotune(reqs, prec, d.x, d.v, d.out, d.params, ws, ws.numel())
+        assert tuned >= 9, tuned
+        plan = cf.RaggedPlan(reqs, prec, 0)
+        for f, n in ((R, 5), (A, 40), (F, 150), (F, 33)):
+            tc = cf.chessfad_ragged_tuned_config(prec, f, n)
+            assert tc is not None and tc[0] in (8, 16) and 1 <= tc[1] <= 32
+            if (f, n) in set(zip(rg.fns.tolist(), rg.ns.tolist())):
+                c, t = cf.chessfad_ragged_plan_group_config(plan.handle, f, n)
+                assert c == tc[0]
+        d.out.fill_(float("nan"))
+        plan.run(d.x, d.v, d.out, d.params)
+        torch.cuda.synchronize()
+        out = d.out.double().cpu().numpy()
+        assert np.all(np.isfinite(out))
+        e = d.errors(out)
+        assert e.max() <= BOUND[prec], (prec, e.max())
+        plan.close()

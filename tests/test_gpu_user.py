@@ -4,13 +4,13 @@ extended-operator function (division, abs, log, tanh, tan, pow, a
 comparison), HVP and Hessian, element by element.
 
 Bounds, per point, normalised by ||H||_F ||v||_2 (||H||_F for a Hessian):
-1e-12 in FP64 and 1e-5 in FP32.  In FP32 the function's own arithmetic is
-plain FP32, as the user wrote it (only the row-times-v sum is compensated):
-its n-term sums (Ackley's Sum x^2 and Sum cos 2 pi x, the Fletcher-Powell
-residuals) carry a relative error up to about n u = 64 * 6e-8 = 4e-6 at the
-sizes tested, inside 1e-5.  Ackley at n <= 2 is the exception: there the
-Hessian's cos(2 pi x) curvature and the sqrt/exp terms nearly cancel, and the
-bound is 1e-4."""
+1e-12 in FP64 and 1e-5 in FP32, for every function and n.  In FP32 the
+function's own arithmetic is plain FP32, as the user wrote it (only the
+row-times-v sum is compensated): its n-term sums (Ackley's Sum x^2 and
+Sum cos 2 pi x, the Fletcher-Powell residuals) carry a relative error up to
+about n u = 64 * 6e-8 = 4e-6 at the sizes tested, inside 1e-5.  At n = 1 the
+Hessian is one entry, a sum of terms that can cancel far below their size,
+and an FP32 handle evaluates it in FP64 (float in and out)."""
 import numpy as np
 import pytest
 
@@ -29,10 +29,6 @@ BOUND = {
 }
 
 
-def bound(prec, fn, n):
-    if prec == cf.FP32_COMP and fn == W.ACKLEY and n <= 2:
-        return 1e-4
-    return BOUND[prec][fn]
 _cache = {}
 
 
@@ -98,7 +94,21 @@ def test_user_sizes(fn, n):
         k = Case(fn, n, 37 if n < 100 else 5, 950 + n, prec)
         for cfg in (PLAIN, None):
             e = k.hvp_err(f.hvp(k.x, k.v, k.params, cfg=cfg))
-            assert e.max() <= bound(prec, fn, n), (prec, cfg, e.max())
+            assert e.max() <= BOUND[prec][fn], (prec, cfg, e.max())
+
+
+@pytest.mark.parametrize("fn", FNS)
+def test_user_fp32_one_variable_many_points(fn):
+    """n = 1 in an FP32 handle over 20000 points, HVP and Hessian, both
+    methods: within 1e-5 everywhere (an FP32 evaluation of the single entry
+    misses it at about 3 % of random Ackley points)."""
+    f = user_fn(fn, 8, cf.FP32_COMP)
+    k = Case(fn, 1, 20000, 990 + fn, cf.FP32_COMP)
+    for cfg in (PLAIN, SYM, None):
+        e = k.hvp_err(f.hvp(k.x, k.v, k.params, cfg=cfg))
+        assert e.max() <= 1e-5, (cfg, e.max())
+        e = k.hess_err(f.hessian(k.x, k.params, cfg=cfg))
+        assert e.max() <= 1e-5, (cfg, e.max())
 
 
 def test_user_equals_builtin_fp64():
