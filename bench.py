@@ -608,19 +608,18 @@ def model_flops_request(fn: int, n: int, c: int) -> float:
 
 def ragged_arm(args, world, dev, stream, flush):
     """The 100000-request uneven batch (three functions, n log-uniform in
-    [2, 512], seed 4) in compensated FP32: one persistent launch per step,
-    replayed from a captured CUDA graph."""
+    [2, 512], seed 4) in compensated FP32: the library's uneven-batch
+    autotuner picks (chunk size, lanes per row) per (function, n range), then
+    one persistent launch per step, replayed from a captured CUDA graph.  The
+    default (untuned) plan is timed once beside it."""
+    import numpy as np
     import torch
 
     import paper_2410_22575_gb300 as cf
     from paper_2410_22575_gb300 import workloads as W
 
     rg = W.make_ragged()
-    c = 16  # the plan's default chunk size for compensated FP32
     reqs = cf.requests(rg.fns, rg.ns, rg.offs, rg.eoffs)
-    t0 = time.perf_counter()
-    plan = cf.RaggedPlan(reqs, cf.FP32_COMP, c)
-    t_plan = time.perf_counter() - t0
     x = torch.tensor(rg.xpack, dtype=torch.float32, device=dev)
     v = torch.tensor(rg.vpack, dtype=torch.float32, device=dev)
     out = torch.empty_like(x)
@@ -628,26 +627,52 @@ def ragged_arm(args, world, dev, stream, flush):
     B = torch.tensor(rg.fp.B, device=dev)
     E = torch.tensor(rg.Epack, device=dev)
     params = cf.fp_params(A, B, E)
-    plan.run(x, v, out, params)  # per-device set-up, outside capture
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        plan.run(x, v, out, params)
-    barrier(world)
-    ms = timed_steps(g.replay, args.ragged_steps, 0, stream, flush)
-    torch.cuda.synchronize()
-    barrier(world)
-    tot = max_over_ranks(world, sum(ms), dev)
-    flops = sum(model_flops_request(int(f), int(n), c) for f, n in zip(rg.fns, rg.ns))
-    per = tot / len(ms)
-    return {"value": world * rg.nreq * len(ms) / (tot * 1e-3), "unit": "HVP/s", "requests": rg.nreq,
-            "steps": len(ms), "warmup": 1, "ms_per_step": per, "precision": "fp32_comp", "csize": c,
+
+    def time_plan(plan, steps):
+        plan.run(x, v, out, params)  # per-device set-up, outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(x, v, out, params)
+        barrier(world)
+        ms = timed_steps(g.replay, steps, 0, stream, flush)
+        torch.cuda.synchronize()
+        barrier(world)
+        return max_over_ranks(world, sum(ms), dev), len(ms)
+
+    default_plan = cf.RaggedPlan(reqs, cf.FP32_COMP, 16)
+    t_default, _ = (None, 0) if args.no_ragged_default else time_plan(default_plan, 1)
+    ws = default_plan.workspace
+    t0 = time.perf_counter()
+    ngroups = cf.chessfad_ragged_autotune(reqs, cf.FP32_COMP, x, v, out, params, ws, ws.numel())
+    t_tune = time.perf_counter() - t0
+    del default_plan, ws
+    t0 = time.perf_counter()
+    plan = cf.RaggedPlan(reqs, cf.FP32_COMP, 0)
+    t_plan = time.perf_counter() - t0
+    tot, steps = time_plan(plan, args.ragged_steps)
+    groups = {}
+    flops = 0.0
+    for f in (0, 1, 2):
+        for b in range(1, 9):
+            lo, hi = 1 << b, min(512, (2 << b) - 1) if b < 8 else 512
+            sel = (rg.fns == f) & (rg.ns >= lo) & (rg.ns <= hi)
+            if not sel.any():
+                continue
+            c, tpr = cf.chessfad_ragged_plan_group_config(plan.handle, f, int(rg.ns[sel][0]))
+            groups[f"{W.FN_NAMES[f]}/n{lo}-{hi}"] = {"csize": c, "threads_per_row": tpr, "requests": int(sel.sum())}
+            flops += sum(model_flops_request(f, int(n), c) for n in rg.ns[sel])
+    per = tot / steps
+    return {"value": world * rg.nreq * steps / (tot * 1e-3), "unit": "HVP/s", "requests": rg.nreq,
+            "steps": steps, "warmup": 1, "ms_per_step": per, "precision": "fp32_comp",
             "launch": "one persistent kernel per step, CUDA graph replay", "tiles": plan.info["ntiles"],
             "method": "plain; symmetric (SC-HESS-VEC) for Fletcher-Powell n >= 128",
+            "tuned_groups": groups, "autotune_seconds": t_tune, "groups_tuned": ngroups,
+            "untuned_ms_per_step": t_default, "untuned_config": "csize 16, default lanes per row",
             "workspace_bytes": plan.info["workspace_bytes"], "plan_seconds": t_plan,
             "model_tflops": flops / (per * 1e-3) / 1e12,
             "_out": out.double().cpu().numpy(), "_x": x.double().cpu().numpy(), "_v": v.double().cpu().numpy(),
-            "_rg": rg, "_c": c}
+            "_rg": rg, "_c": 16}
 
 
 # ------------------------------------------------------------------ oracle leg
@@ -1238,6 +1263,7 @@ def main():
     ap.add_argument("--no-workloads", action="store_true", help="skip the other named workloads")
     ap.add_argument("--workload-steps", type=int, default=5, help="timed steps per row of the workloads block")
     ap.add_argument("--ragged-steps", type=int, default=1)
+    ap.add_argument("--no-ragged-default", action="store_true", help="skip timing the untuned uneven-batch plan")
     ap.add_argument("--ragged-cpu-cap", type=float, default=3e9,
                     help="uneven-batch CPU baseline: model-flop cap of the sampled requests")
     ap.add_argument("--kernel-only", action="store_true", help="run only the sweep kernel (for ncu)")
