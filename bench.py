@@ -122,7 +122,7 @@ def algorithmic_bytes(n: int, prec: int, kind: str) -> int:
 # Sources that define the batched sweep kernels: the executed-instruction
 # counts and DRAM traffic in profiles/counts.json are used only while these
 # are unchanged since the capture.
-KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "point.cuh", "point.h", "k_*.cu")
+KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "point.cuh", "instances.cu")
 
 
 def kernel_source_hash() -> str:

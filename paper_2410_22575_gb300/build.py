@@ -1,8 +1,9 @@
 """Build the CUDA library ``_build/libchessfad.so`` for sm_103a, in-tree.
 
 Each translation unit under ``csrc/`` is compiled in parallel with
-``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` and the objects
-are linked into one shared library with the CUDA runtime linked statically.
+``nvcc -gencode arch=compute_103a,code=sm_103a -O3 -lineinfo`` (``instances.cu``
+once per (function, precision) slice) and the objects are linked into one
+shared library with the CUDA runtime linked statically.
 A rebuild happens only when a source or the public header is newer than the
 library.  Usage: ``python -m paper_2410_22575_gb300.build [--force]``.
 """
@@ -32,8 +33,27 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libchessfad")
 
 
+# instances.cu is compiled once per (function, precision) slice.
+SLICED = "instances.cu"
+SLICES = [(fn, f64) for fn in (0, 1, 2) for f64 in (0, 1)]
+
+
 def sources() -> list[str]:
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def compile_units() -> list[tuple[str, list[str], str]]:
+    """(source, extra flags, object name) of every translation unit."""
+    units = []
+    for src in sources():
+        base = os.path.basename(src)[:-3]
+        if os.path.basename(src) == SLICED:
+            for fn, f64 in SLICES:
+                units.append((src, [f"-DCHESSFAD_SLICE_FN={fn}", f"-DCHESSFAD_SLICE_F64={f64}"],
+                              f"{base}_{fn}_{f64}.o"))
+        else:
+            units.append((src, [], base + ".o"))
+    return units
 
 
 def _deps() -> list[str]:
@@ -71,9 +91,10 @@ def write_embedded() -> str:
     return path
 
 
-def _compile(src: str, verbose_ptxas: bool) -> tuple[str, str]:
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
-    cmd = ([nvcc()] + ARCH + FLAGS + ["-I", OUT] + (["-Xptxas", "-v"] if verbose_ptxas else [])
+def _compile(unit: tuple[str, list[str], str], verbose_ptxas: bool) -> tuple[str, str]:
+    src, extra, name = unit
+    obj = os.path.join(OUT, name)
+    cmd = ([nvcc()] + ARCH + FLAGS + extra + ["-I", OUT] + (["-Xptxas", "-v"] if verbose_ptxas else [])
            + ["-c", src, "-o", obj])
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
@@ -86,11 +107,14 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
         return LIB
     os.makedirs(OUT, exist_ok=True)
     write_embedded()
-    srcs = sources()
-    jobs = jobs or min(len(srcs), max(1, os.cpu_count() or 1))
+    units = compile_units()
+    # the slowest units first, so the parallel build ends sooner
+    order = {"ragged": 0, "instances": 1}
+    units.sort(key=lambda u: order.get(os.path.basename(u[0])[:-3], 2))
+    jobs = jobs or min(len(units), max(1, os.cpu_count() or 1))
     logs = []
     with cf.ThreadPoolExecutor(jobs) as ex:
-        for obj, log in ex.map(lambda s: _compile(s, verbose_ptxas), srcs):
+        for obj, log in ex.map(lambda u: _compile(u, verbose_ptxas), units):
             logs.append((obj, log))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in logs] + ["-cudart", "static", "-ldl"]

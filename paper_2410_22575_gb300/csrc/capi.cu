@@ -13,7 +13,6 @@
 
 #include "../../include/chessfad.h"
 #include "dispatch.h"
-#include "point.h"
 
 namespace chessfad {
 
@@ -222,6 +221,7 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
     if (fn == CHESSFAD_FLETCHER_POWELL && a.mt % fp_mb(c.csize) != 0) return CHESSFAD_ERR_CONFIG;
     cudaError_t e = cudaErrorInvalidValue;
     const bool f64 = (prec == CHESSFAD_FP64);
+    const SliceOps &ops = slice(fn, f64);
     const bool sym = c.method == CHESSFAD_METHOD_SYMMETRIC || c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE;
     if (sym && !(!f64 && n == 1)) {
         const bool sparse = c.method == CHESSFAD_METHOD_SYMMETRIC_SPARSE;
@@ -230,11 +230,7 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         a.tpp = c.threads_per_point;
         auto bytes = [&](int ppb) {
             a.maxpts = ppb;
-            switch (fn) {
-            case CHESSFAD_ROSENBROCK: return f64 ? smem_rosenbrock_f64_sym(c.csize, hvp, a) : smem_rosenbrock_f32c_sym(c.csize, hvp, a);
-            case CHESSFAD_ACKLEY: return f64 ? smem_ackley_f64_sym(c.csize, hvp, a) : smem_ackley_f32c_sym(c.csize, hvp, a);
-            default: return f64 ? smem_fp_f64_sym(c.csize, hvp, a) : smem_fp_f32c_sym(c.csize, hvp, a);
-            }
+            return ops.sym_smem(c.csize, hvp, a);
         };
         int ppb = (int)std::min<long long>(batch, std::max(1, c.block_threads / c.threads_per_point));
         const size_t kBudget = 200 * 1024;
@@ -249,33 +245,7 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         }
         if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
         a.maxpts = ppb;
-        if (sparse) {
-            switch (fn) {
-            case CHESSFAD_ROSENBROCK:
-                e = f64 ? launch_rosenbrock_f64_sym_sparse(c.csize, hvp, a, stream)
-                        : launch_rosenbrock_f32c_sym_sparse(c.csize, hvp, a, stream);
-                break;
-            case CHESSFAD_ACKLEY:
-                e = f64 ? launch_ackley_f64_sym_sparse(c.csize, hvp, a, stream)
-                        : launch_ackley_f32c_sym_sparse(c.csize, hvp, a, stream);
-                break;
-            case CHESSFAD_FLETCHER_POWELL:
-                e = f64 ? launch_fp_f64_sym_sparse(c.csize, hvp, a, stream) : launch_fp_f32c_sym_sparse(c.csize, hvp, a, stream);
-                break;
-            }
-        } else {
-            switch (fn) {
-            case CHESSFAD_ROSENBROCK:
-                e = f64 ? launch_rosenbrock_f64_sym(c.csize, hvp, a, stream) : launch_rosenbrock_f32c_sym(c.csize, hvp, a, stream);
-                break;
-            case CHESSFAD_ACKLEY:
-                e = f64 ? launch_ackley_f64_sym(c.csize, hvp, a, stream) : launch_ackley_f32c_sym(c.csize, hvp, a, stream);
-                break;
-            case CHESSFAD_FLETCHER_POWELL:
-                e = f64 ? launch_fp_f64_sym(c.csize, hvp, a, stream) : launch_fp_f32c_sym(c.csize, hvp, a, stream);
-                break;
-            }
-        }
+        e = sparse ? ops.sym_sparse(c.csize, hvp, a, stream) : ops.sym(c.csize, hvp, a, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }
     if (c.method == CHESSFAD_METHOD_POINT && !(!f64 && n == 1)) {
@@ -285,51 +255,29 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         a.tpp = 1;
         auto bytes = [&](int ppb) {
             a.maxpts = ppb;
-            return f64 ? smem_point_f64(fn, c.csize, hvp, a) : smem_point_f32c(fn, c.csize, hvp, a);
+            return ops.point_smem(c.csize, hvp, a);
         };
         int ppb = c.block_threads;
         while (ppb > 32 && bytes(ppb) > 200 * 1024) ppb -= 32;
         if (bytes(ppb) > 200 * 1024) return CHESSFAD_ERR_SIZE;
         a.maxpts = ppb;
-        e = f64 ? launch_point_f64(fn, c.csize, hvp, a, stream) : launch_point_f32c(fn, c.csize, hvp, a, stream);
+        e = ops.point(c.csize, hvp, a, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }
     if (!f64 && n == 1) {
         // One variable: compute in FP64 (float I/O), see dispatch.h.
         a.nch = 1;
-        switch (fn) {
-        case CHESSFAD_ROSENBROCK: e = launch_rosenbrock_f64io32(hvp, a, c.block_threads, stream); break;
-        case CHESSFAD_ACKLEY: e = launch_ackley_f64io32(hvp, a, c.block_threads, stream); break;
-        case CHESSFAD_FLETCHER_POWELL: e = launch_fp_f64io32(hvp, a, c.block_threads, stream); break;
-        }
+        e = ops.sweep_f64io32(hvp, a, c.block_threads, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }
-    switch (fn) {
-    case CHESSFAD_ROSENBROCK:
-        e = f64 ? launch_rosenbrock_f64(c.csize, hvp, a, c.block_threads, stream)
-                : launch_rosenbrock_f32c(c.csize, hvp, a, c.block_threads, stream);
-        break;
-    case CHESSFAD_ACKLEY:
-        e = f64 ? launch_ackley_f64(c.csize, hvp, a, c.block_threads, stream)
-                : launch_ackley_f32c(c.csize, hvp, a, c.block_threads, stream);
-        break;
-    case CHESSFAD_FLETCHER_POWELL:
-        e = f64 ? launch_fp_f64(c.csize, hvp, a, c.block_threads, stream)
-                : launch_fp_f32c(c.csize, hvp, a, c.block_threads, stream);
-        break;
-    }
+    e = ops.sweep(c.csize, hvp, a, c.block_threads, stream);
     return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
 }
 
 static cudaError_t kernel_attr(int fn, int prec, int csize, bool hvp, cudaFuncAttributes *fa)
 {
-    const bool f64 = (prec == CHESSFAD_FP64);
-    switch (fn) {
-    case CHESSFAD_ROSENBROCK: return f64 ? attr_rosenbrock_f64(csize, hvp, fa) : attr_rosenbrock_f32c(csize, hvp, fa);
-    case CHESSFAD_ACKLEY: return f64 ? attr_ackley_f64(csize, hvp, fa) : attr_ackley_f32c(csize, hvp, fa);
-    case CHESSFAD_FLETCHER_POWELL: return f64 ? attr_fp_f64(csize, hvp, fa) : attr_fp_f32c(csize, hvp, fa);
-    }
-    return cudaErrorInvalidValue;
+    if (fn < 0 || fn > 2) return cudaErrorInvalidValue;
+    return slice(fn, prec == CHESSFAD_FP64).attr(csize, hvp, fa);
 }
 
 static int run(int fn, int n, long long batch, const chessfad_config *cfg, int csize_hint, const void *x,
