@@ -849,9 +849,8 @@ def reference_arm(args):
 
 # ------------------------------------------------------------------ executed-instruction counts
 # The kernels whose executed FP instructions (and DRAM bytes) the roofline
-# reports: for each named workload and precision the symmetric HVP at every
-# chunk size the autotuner may pick, the plain method at the stated c = 4 of
-# Rosenbrock n=16, and the Hessians of Rosenbrock n=16 and n=256.  Counts are
+# reports: for each named workload and precision both methods at every chunk
+# size the autotuner may pick (profile_set).  Counts are
 # per point: the per-point work of these kernels does not depend on the number
 # of points, threads per point or points per CTA, so a capture on a prefix of
 # the batch scales to the full batch by the number of points.
@@ -861,21 +860,22 @@ PROFILE_BATCH = {("ackley_n64", 0): 16384, ("ackley_n64", 1): 16384, ("rosenbroc
 
 
 def profile_set():
+    """Every (workload, precision, kind, method, chunk size) the bench's
+    autotuned or stated configurations can land on: both methods, chunk sizes
+    2..32 up to the next power of two of n (spilling kernels are skipped at
+    run time), HVPs everywhere and Hessians of the Rosenbrock workloads."""
     from paper_2410_22575_gb300 import workloads as W
 
     out = []
     for name in ("ackley_n64", "rosenbrock_n16", "fletcher_powell_n32", "rosenbrock_n256"):
         fn, n, _, _ = W.WORKLOADS[name]
+        kinds = ("hvp", "hessian") if name in ("rosenbrock_n16", "rosenbrock_n256") else ("hvp",)
         for prec in (0, 1):
-            cs = [c for c in (2, 4, 8, 16) if c <= max(1, 1 << (n - 1).bit_length())]
-            for c in cs:
-                out.append((name, prec, "hvp", "symmetric", c))
-            if name == "rosenbrock_n16":
-                out.append((name, prec, "hvp", "plain", 4))
-            if name in ("rosenbrock_n16", "rosenbrock_n256"):
-                for c in cs:
-                    out.append((name, prec, "hessian", "symmetric", c))
-                out.append((name, prec, "hessian", "plain", 4))
+            cs = [c for c in (2, 4, 8, 16, 32) if c <= max(1, 1 << (n - 1).bit_length())]
+            for kind in kinds:
+                for method in ("symmetric", "plain"):
+                    for c in cs:
+                        out.append((name, prec, kind, method, c))
     return out
 
 

@@ -307,16 +307,19 @@ CHESSFAD_API int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, in
                                                    int *threads_per_row);
 
 /* Autotune the uneven batch: for every (function, n range) group of the
- * requests (ranges as for chessfad_ragged_plan_create), time the persistent
+ * requests (ranges as for chessfad_ragged_plan_create), run the persistent
  * kernel on a sample of the group's requests (in table order, enough rows to
  * fill the GPU about four times) for every chunk size (16, 8) and lanes per
- * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values), and
- * store the fastest per (prec, function, n range) in the process-wide table
+ * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values),
+ * measuring the SM cycles its tiles take, summed over the CTAs (the group's
+ * throughput inside a large mixed run, free of the small sample's own tail),
+ * and store the cheapest per (prec, function, n range) in the process-wide
+ * table
  * that chessfad_ragged_plan_create(..., csize = 0, ...) reads.  xpack, vpack,
  * outpack, params as for chessfad_hvp_ragged (outpack of the sampled requests
  * is overwritten); workspace: device scratch of workspace_bytes (candidates
- * whose trial plan needs more are skipped; the workspace of a plan of all
- * the requests is enough).  *groups_tuned (may be NULL) receives the number
+ * whose trial plan needs more, plus 256 bytes for the cycle counter, are
+ * skipped; the workspace of a plan of all the requests is usually enough).  *groups_tuned (may be NULL) receives the number
  * of groups stored.  Synchronises `stream`; allocates no device memory. */
 CHESSFAD_API int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int prec, const void *xpack,
                                           const void *vpack, void *outpack, const chessfad_fp_params *params,

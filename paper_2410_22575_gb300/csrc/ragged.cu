@@ -73,6 +73,7 @@ struct RaggedArgs {
     int *counter;
     int *done;               // per request: tiles completed (symmetric requests)
     double *slots;           // per symmetric tile: its partial row vector (FP64)
+    unsigned long long *busy;  // autotuning: SM cycles spent in tiles, summed (null otherwise)
     int ntiles;
     int ld;
 };
@@ -267,9 +268,17 @@ __global__ void __launch_bounds__(kRaggedBlock, 1) ragged_kernel(const RaggedArg
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_tile;
+    long long t_start = -1;  // thread 0, autotuning only: start of the current tile
     for (;;) {
         __syncthreads();  // the previous tile is done with shared memory and s_tile
-        if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1);
+        if (threadIdx.x == 0) {
+            if (a.busy) {
+                const long long now = clock64();
+                if (t_start >= 0) atomicAdd(a.busy, (unsigned long long)(now - t_start));
+                t_start = now;
+            }
+            s_tile = atomicAdd(a.counter, 1);
+        }
         __syncthreads();
         const int t = s_tile;
         if (t >= a.ntiles) break;
@@ -590,9 +599,10 @@ RaggedArgs ragged_args(const chessfad_ragged_plan_s *plan, unsigned char *ws, co
 }
 
 int run_plan(chessfad_ragged_plan_s *plan, unsigned char *ws, const void *xpack, const void *vpack, void *outpack,
-             const chessfad_fp_params *params, cudaStream_t s)
+             const chessfad_fp_params *params, cudaStream_t s, unsigned long long *busy = nullptr)
 {
-    const RaggedArgs a = ragged_args(plan, ws, xpack, vpack, outpack, params);
+    RaggedArgs a = ragged_args(plan, ws, xpack, vpack, outpack, params);
+    a.busy = busy;
     const cudaError_t e =
         plan->prec == CHESSFAD_FP64 ? launch_ragged<double>(plan, a, s) : launch_ragged<float>(plan, a, s);
     return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
@@ -711,12 +721,6 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
     std::map<std::pair<int, int>, std::vector<long long>> groups;
     for (long long q = 0; q < nreq; ++q) groups[{reqs[q].fn, n_bucket(reqs[q].n)}].push_back(q);
 
-    cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return CHESSFAD_ERR_CUDA;
-    if (cudaEventCreate(&e1) != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return CHESSFAD_ERR_CUDA;
-    }
     int rc = CHESSFAD_SUCCESS;
     long long tuned = 0;
     for (auto &g : groups) {
@@ -749,7 +753,7 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
             }
         }
         GroupCfg best;
-        float best_ms = INFINITY;
+        float best_ms = INFINITY;  // the objective: summed SM cycles of the sample's tiles
         for (const GroupCfg &c : cands) {
             std::map<std::pair<int, int>, GroupCfg> force;
             force[{fn, bucket}] = c;
@@ -757,8 +761,10 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
             opt.force = &force;
             chessfad_ragged_plan_s trial;
             if (build_plan(sample.data(), (long long)sample.size(), prec, opt, &trial) != CHESSFAD_SUCCESS) continue;
-            if (trial.total > workspace_bytes) continue;
+            // the busy-cycle counter after the trial plan's workspace
+            if (trial.total + 256 > workspace_bytes) continue;
             unsigned char *ws = static_cast<unsigned char *>(workspace);
+            unsigned long long *busy = reinterpret_cast<unsigned long long *>(ws + trial.total);
             if (cudaMemcpyAsync(ws, trial.image.data(), trial.table_bytes, cudaMemcpyHostToDevice, stream) !=
                 cudaSuccess) {
                 rc = CHESSFAD_ERR_CUDA;
@@ -768,15 +774,21 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
                 cudaGetLastError();
                 continue;
             }
-            cudaEventRecord(e0, stream);
-            for (int k = 0; k < 2; ++k) run_plan(&trial, ws, xpack, vpack, outpack, params, stream);
-            cudaEventRecord(e1, stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
+            // The objective is the SM time the group's tiles take, summed over
+            // the CTAs (one CTA per SM): the throughput the group gets inside
+            // a large mixed run, free of the sample's own tail.
+            if (cudaMemsetAsync(busy, 0, sizeof(unsigned long long), stream) != cudaSuccess ||
+                run_plan(&trial, ws, xpack, vpack, outpack, params, stream, busy) != CHESSFAD_SUCCESS) {
                 rc = CHESSFAD_ERR_CUDA;
                 break;
             }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
+            unsigned long long cycles = 0;
+            if (cudaMemcpyAsync(&cycles, busy, sizeof(cycles), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+                cudaStreamSynchronize(stream) != cudaSuccess) {
+                rc = CHESSFAD_ERR_CUDA;
+                break;
+            }
+            const float ms = (float)cycles;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -789,8 +801,6 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
             ++tuned;
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (groups_tuned) *groups_tuned = tuned;
     return rc;
 }

@@ -426,6 +426,35 @@ struct ListPoints {
     __device__ __forceinline__ const double *e(long long p) const { return Epack + eoffs[list[p]]; }
 };
 
+// Copy src[0 .. cnt) (global memory, T-aligned) to dst (shared memory): the
+// 16-byte-aligned middle of the range with vector loads (float4 / double2),
+// the ragged ends element by element.  Every thread of the block calls it.
+template <typename T>
+__device__ __forceinline__ void stage_range(T *dst, const T *__restrict__ src, int cnt)
+{
+    using Vec = typename std::conditional<sizeof(T) == 8, double2, float4>::type;
+    constexpr int V = (int)(sizeof(Vec) / sizeof(T));
+    const int mis = (int)(((16 - ((size_t)src & 15)) & 15) / sizeof(T));
+    const int head = mis < cnt ? mis : cnt;
+    const int nvec = (cnt - head) / V;
+    for (int e = threadIdx.x; e < head; e += blockDim.x) dst[e] = src[e];
+    const Vec *sv = reinterpret_cast<const Vec *>(src + head);
+    for (int w = threadIdx.x; w < nvec; w += blockDim.x) {
+        const Vec q = sv[w];
+        T *d = dst + head + w * V;
+        if constexpr (V == 2) {
+            d[0] = q.x;
+            d[1] = q.y;
+        } else {
+            d[0] = q.x;
+            d[1] = q.y;
+            d[2] = q.z;
+            d[3] = q.w;
+        }
+    }
+    for (int e = head + nvec * V + threadIdx.x; e < cnt; e += blockDim.x) dst[e] = src[e];
+}
+
 // Stage the x (and v) of the points p0 .. p0+npts-1 into shared memory and
 // build their per-point value tables (the FP64 islands).  Every thread of the
 // block calls it; it ends with the block synchronised.
@@ -441,11 +470,17 @@ __device__ __forceinline__ void point_prologue(const Job &a, const PM &pm, unsig
         const IO *X = reinterpret_cast<const IO *>(a.x);
         const IO *V = reinterpret_cast<const IO *>(a.v);
         const int cnt = npts * n;
-        for (int e = tid; e < cnt; e += blockDim.x) {
-            const int q = e / n, k = e - q * n;
-            const long long o = pm.off(p0 + q) + k;
-            xs[e] = (T)X[o];
-            if (HVP) vs[e] = (T)V[o];
+        if constexpr (std::is_same<PM, ContigPoints>::value && std::is_same<IO, T>::value) {
+            // the block's points are one contiguous range of x and v
+            stage_range<T>(xs, X + pm.off(p0), cnt);
+            if (HVP) stage_range<T>(vs, V + pm.off(p0), cnt);
+        } else {
+            for (int e = tid; e < cnt; e += blockDim.x) {
+                const int q = e / n, k = e - q * n;
+                const long long o = pm.off(p0 + q) + k;
+                xs[e] = (T)X[o];
+                if (HVP) vs[e] = (T)V[o];
+            }
         }
     }
     __syncthreads();
