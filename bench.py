@@ -207,6 +207,7 @@ def roofline_entry(counts: dict, key: str, units: int, ms: float, prec: int, pea
         "algorithmic_bytes_per_launch": algo,
         "dram_gbs_algorithmic": algo / (ms * 1e-3) / 1e9,
         "dram_gbs_measured_traffic": None if traffic is None else traffic / (ms * 1e-3) / 1e9,
+        "issue_active_pct_ncu": None if ent is None else ent.get("issue_active_pct"),
         "counts_key": key, "counts_present": ent is not None,
     }
 
@@ -922,6 +923,7 @@ def profile_kernels(args):
 
 
 NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum,"
+               "smsp__issue_active.avg.pct_of_peak_sustained_active,smsp__inst_executed.sum,"
                "smsp__sass_thread_inst_executed_op_ffma_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_fadd_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum,"
@@ -1002,6 +1004,8 @@ def ingest_ncu(args):
             "fp64_flops_per_unit": (2 * g("dfma") + g("dadd") + g("dmul")) / u,
             "dram_bytes_per_unit": None if math.isnan(dram) else dram / u,
             "duration_ns_captured": l.get("gpu__time_duration.sum"),
+            "issue_active_pct": l.get("smsp__issue_active.avg.pct_of_peak_sustained_active"),
+            "warp_instructions_per_unit": l.get("smsp__inst_executed.sum", float("nan")) / u,
         }
     doc = {"source_hash": keys["source_hash"],
            "note": ("per point ('unit'): executed flops = 2 x FMA + ADD + MUL thread instructions (FP32 and "
@@ -1013,6 +1017,28 @@ def ingest_ncu(args):
     with open(COUNTS_FILE, "w") as f:
         json.dump(doc, f, indent=1, sort_keys=True)
     print(f"{len(kernels)} kernels -> {COUNTS_FILE}")
+    # a markdown table of the capture (executed against model flops, DRAM
+    # bytes against algorithmic bytes, per point)
+    from paper_2410_22575_gb300 import workloads as W
+
+    print("| kernel key | kernel | executed flop/pt | model / executed | issue active % | DRAM B/pt | "
+          "algorithmic B/pt | ncu time (ms) |")
+    print("|---|---|---|---|---|---|---|---|")
+    for key in sorted(kernels):
+        e = kernels[key]
+        name, prec_s, kind, method, c = key.split("/")
+        fn, n, _, _ = W.WORKLOADS[name]
+        prec = 0 if prec_s == "fp64" else 1
+        c = int(c[1:])
+        sym = method == "symmetric"
+        mf = (model_flops_hvp if kind == "hvp" else model_flops_hessian)(fn, n, c, sym)
+        kn = kernel_name(method, prec, c, fn, kind)
+        dram = e["dram_bytes_per_unit"]
+        ia = e.get("issue_active_pct")
+        print(f"| {key} | {kn} | {e['executed_flops_per_unit']:.4g} | {mf / e['executed_flops_per_unit']:.2f} | "
+              f"{'-' if ia is None else f'{ia:.1f}'} | "
+              f"{'-' if dram is None else f'{dram:.0f}'} | {algorithmic_bytes(n, prec, kind)} | "
+              f"{(e['duration_ns_captured'] or 0) / 1e6:.2f} |")
 
 
 def kernel_only(args):

@@ -2,11 +2,11 @@
 // the ALU-bound sweep kernels).  Every thread runs NCH independent dependent
 // chains a = fma(a, m, b) over all SMs; one FMA counts as two flops.  The
 // result is folded into a never-taken store so the chains cannot be removed.
-// Several (chains per thread, CTAs per SM) shapes are timed and the best is
-// reported, so the number is the pipe's throughput rather than one shape's
-// latency or occupancy limit.  Thread 0 of CTA 0 reads the SM cycle counter
-// and the global nanosecond timer around its loop, which gives the SM clock
-// the run actually saw.
+// Several (chains per thread, CTAs per SM) shapes, with shared or per-chain
+// operands, are timed and the best is reported, so the number is the pipe's
+// throughput rather than one shape's latency, occupancy or operand limit.
+// Thread 0 of CTA 0 reads the SM cycle counter and the global nanosecond
+// timer around its loop, which gives the SM clock the run actually saw.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -59,14 +59,52 @@ __global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T seed)
     }
 }
 
+// The same with a multiplier and an addend per chain (held in registers,
+// not literals), so no two chains read the same operand registers.
+template <typename T, int NCH>
+__global__ void __launch_bounds__(256) fma_peak_kernel_ops(int iters, T seed)
+{
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long c0 = 0, t0 = 0;
+    if (timer) {
+        t0 = global_ns();
+        c0 = clock64();
+    }
+    T a[NCH], m[NCH], b[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        a[c] = seed + T(c) * T(1e-3) + T(threadIdx.x) * T(1e-7);
+        m[c] = T(0.9999999) - T(c) * T(1e-9) - T(threadIdx.x & 7) * T(1e-10);
+        b[c] = T(1e-7) + T(c) * T(1e-9);
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) a[c] = fma(a[c], m[c], b[c]);
+        }
+    }
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) s += a[c];
+    if (s == T(-12345.0)) g_peak_sink<T> = s;
+    if (timer) {
+        const unsigned long long c1 = clock64();
+        const unsigned long long t1 = global_ns();
+        g_peak_clk[0] = c1 - c0;
+        g_peak_clk[1] = t1 - t0;
+    }
+}
+
 struct PeakResult {
     double flops = 0.0;
     double sm_mhz = 0.0;
 };
 
-template <typename T, int NCH>
+template <typename T, int NCH, bool OPS = false>
 static int measure(int iters, int blocks_per_sm, PeakResult *best)
 {
+    auto kern = OPS ? fma_peak_kernel_ops<T, NCH> : fma_peak_kernel<T, NCH>;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
@@ -77,11 +115,11 @@ static int measure(int iters, int blocks_per_sm, PeakResult *best)
         cudaEventDestroy(e0);
         return CHESSFAD_ERR_CUDA;
     }
-    fma_peak_kernel<T, NCH><<<blocks, threads>>>(std::max(1, iters / 16), T(1));
+    kern<<<blocks, threads>>>(std::max(1, iters / 16), T(1));
     int rc = CHESSFAD_SUCCESS;
     for (int rep = 0; rep < 3 && rc == CHESSFAD_SUCCESS; ++rep) {
         cudaEventRecord(e0);
-        fma_peak_kernel<T, NCH><<<blocks, threads>>>(iters, T(1));
+        kern<<<blocks, threads>>>(iters, T(1));
         cudaEventRecord(e1);
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
             rc = CHESSFAD_ERR_CUDA;
@@ -112,7 +150,8 @@ static int peak(int prec, PeakResult *r)
     if (prec == CHESSFAD_FP32_COMP) {
         // FP32: 128 lanes per SM; 8 chains at 8 CTAs of 256 per SM saturate.
         if ((rc = measure<float, 8>(40000, 8, r))) return rc;
-        return measure<float, 16>(20000, 4, r);
+        if ((rc = measure<float, 16>(20000, 4, r))) return rc;
+        return measure<float, 8, true>(40000, 8, r);
     }
     if (prec == CHESSFAD_FP64) {
         // FP64: few lanes per SM and a long pipe: more chains per thread, and
@@ -120,7 +159,9 @@ static int peak(int prec, PeakResult *r)
         if ((rc = measure<double, 8>(800, 8, r))) return rc;
         if ((rc = measure<double, 16>(400, 8, r))) return rc;
         if ((rc = measure<double, 16>(800, 4, r))) return rc;
-        return measure<double, 32>(400, 4, r);
+        if ((rc = measure<double, 32>(400, 4, r))) return rc;
+        if ((rc = measure<double, 8, true>(800, 8, r))) return rc;
+        return measure<double, 16, true>(400, 4, r);
     }
     return CHESSFAD_ERR_PRECISION;
 }
