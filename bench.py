@@ -660,8 +660,10 @@ def ragged_arm(args, world, dev, stream, flush):
             sel = (rg.fns == f) & (rg.ns >= lo) & (rg.ns <= hi)
             if not sel.any():
                 continue
-            c, tpr = cf.chessfad_ragged_plan_group_config(plan.handle, f, int(rg.ns[sel][0]))
-            groups[f"{W.FN_NAMES[f]}/n{lo}-{hi}"] = {"csize": c, "threads_per_row": tpr, "requests": int(sel.sum())}
+            c, tpr, mt = cf.chessfad_ragged_plan_group_config(plan.handle, f, int(rg.ns[sel][0]))
+            groups[f"{W.FN_NAMES[f]}/n{lo}-{hi}"] = {"csize": c, "threads_per_row": tpr, "requests": int(sel.sum()),
+                                                    **({"ab_tile_rows_at_n": [int(rg.ns[sel][0]), mt]}
+                                                       if f == 2 else {})}
             flops += sum(model_flops_request(f, int(n), c) for n in rg.ns[sel])
     per = tot / steps
     return {"value": world * rg.nreq * steps / (tot * 1e-3), "unit": "HVP/s", "requests": rg.nreq,

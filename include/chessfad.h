@@ -302,16 +302,20 @@ CHESSFAD_API int chessfad_ragged_plan_destroy(chessfad_ragged_plan plan);
 CHESSFAD_API int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes, long long *ntiles,
                                            size_t *smem_bytes);
 
-/* The chunk size and lanes per row the plan uses for requests of function fn
- * and size n (CHESSFAD_ERR_SIZE if it holds no such request).  Host only. */
+/* The chunk size, lanes per row and Fletcher-Powell A/B tile height (rows of
+ * A and B staged per shared-memory tile; 8 for the other functions) the plan
+ * uses for requests of function fn and size n (CHESSFAD_ERR_SIZE if it holds
+ * no such request).  Any output pointer may be NULL.  Host only. */
 CHESSFAD_API int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, int fn, int n, int *csize,
-                                                   int *threads_per_row);
+                                                   int *threads_per_row, int *tile_rows);
 
 /* Autotune the uneven batch: for every (function, n range) group of the
  * requests (ranges as for chessfad_ragged_plan_create), run the persistent
  * kernel on a sample of the group's requests (in table order, enough rows to
- * fill the GPU about four times) for every chunk size (16, 8) and lanes per
- * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values),
+ * fill the GPU about four times) for every chunk size (16, 8), lanes per
+ * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values) and,
+ * for Fletcher-Powell, shared-memory budget of the A/B row tiles (48 or 144
+ * KiB, where they differ in tile height),
  * measuring the SM cycles its tiles take, summed over the CTAs (the group's
  * throughput inside a large mixed run, free of the small sample's own tail),
  * and store the cheapest per (prec, function, n range) in the process-wide
@@ -327,9 +331,11 @@ CHESSFAD_API int chessfad_ragged_autotune(const chessfad_request *reqs, long lon
                                           void *workspace, size_t workspace_bytes, chessfad_stream_t stream,
                                           long long *groups_tuned);
 
-/* The tuned (chunk size, lanes per row) of (prec, fn, n's range), or
- * CHESSFAD_ERR_CONFIG if that group has not been tuned.  Host only. */
-CHESSFAD_API int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threads_per_row);
+/* The tuned (chunk size, lanes per row, A/B tile budget in KiB) of (prec,
+ * fn, n's range), or CHESSFAD_ERR_CONFIG if that group has not been tuned.
+ * Any output pointer may be NULL.  Host only. */
+CHESSFAD_API int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threads_per_row,
+                                              int *ab_kib);
 
 /* Copy the plan's tables into a caller-allocated device workspace of at least
  * workspace_bytes (cudaMemcpyAsync on stream from the plan's host memory;

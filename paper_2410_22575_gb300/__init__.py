@@ -91,9 +91,11 @@ def load(build_if_missing: bool = True):
         lib.chessfad_ragged_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(L),
                                                   ctypes.POINTER(ctypes.c_size_t)]
         lib.chessfad_ragged_plan_upload.argtypes = [P, P, ctypes.c_size_t, P]
-        lib.chessfad_ragged_plan_group_config.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.chessfad_ragged_plan_group_config.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                                          ctypes.POINTER(I)]
         lib.chessfad_ragged_autotune.argtypes = [P, L, I, P, P, P, P, P, ctypes.c_size_t, P, ctypes.POINTER(L)]
-        lib.chessfad_ragged_tuned_config.argtypes = [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.chessfad_ragged_tuned_config.argtypes = [I, I, I, ctypes.POINTER(I), ctypes.POINTER(I),
+                                                     ctypes.POINTER(I)]
         lib.chessfad_hvp_ragged.argtypes = [P, P, P, P, P, P, ctypes.c_size_t, P]
         lib.chessfad_hvp_ragged_noalloc.argtypes = [P, P, P, P, P, P]
         lib.chessfad_hvp_ragged_noalloc.restype = I
@@ -351,11 +353,12 @@ def chessfad_hvp_ragged(plan, xpack, vpack, outpack, params, workspace, workspac
                                       workspace_bytes, _stream(stream))
 
 
-def chessfad_ragged_plan_group_config(plan, fn, n) -> tuple[int, int]:
-    c, t = ctypes.c_int(), ctypes.c_int()
-    _check(load().chessfad_ragged_plan_group_config(plan, fn, n, ctypes.byref(c), ctypes.byref(t)),
+def chessfad_ragged_plan_group_config(plan, fn, n) -> tuple[int, int, int]:
+    """(csize, threads_per_row, A/B tile rows) of the plan's (fn, n) group."""
+    c, t, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().chessfad_ragged_plan_group_config(plan, fn, n, ctypes.byref(c), ctypes.byref(t), ctypes.byref(m)),
            "chessfad_ragged_plan_group_config")
-    return c.value, t.value
+    return c.value, t.value, m.value
 
 
 def chessfad_ragged_autotune(reqs, prec, xpack, vpack, outpack, params, workspace, workspace_bytes,
@@ -371,10 +374,11 @@ def chessfad_ragged_autotune(reqs, prec, xpack, vpack, outpack, params, workspac
 
 
 def chessfad_ragged_tuned_config(prec, fn, n):
-    """(csize, threads_per_row) tuned for (prec, fn, n's range), or None."""
-    c, t = ctypes.c_int(), ctypes.c_int()
-    st = load().chessfad_ragged_tuned_config(prec, fn, n, ctypes.byref(c), ctypes.byref(t))
-    return None if st != SUCCESS else (c.value, t.value)
+    """(csize, threads_per_row, A/B tile KiB) tuned for (prec, fn, n's range),
+    or None."""
+    c, t, a = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = load().chessfad_ragged_tuned_config(prec, fn, n, ctypes.byref(c), ctypes.byref(t), ctypes.byref(a))
+    return None if st != SUCCESS else (c.value, t.value, a.value)
 
 
 def chessfad_hvp_ragged_noalloc(plan, xpack, vpack, outpack, params=None, stream=None) -> int:

@@ -339,10 +339,13 @@ double sweep_cost(int fn, int n, int C)
     }
 }
 
-int fp_tile_rows_ragged(int n, int prec, int mb)
+// Rows of A and B per shared-memory tile of the Fletcher-Powell sweep: as
+// many as fit `budget` bytes (both matrices), a multiple of 8 and of mb, at
+// most n rounded up to 8.
+int fp_tile_rows_ragged(int n, int prec, int mb, size_t budget)
 {
     const size_t esz = (prec == CHESSFAD_FP64) ? 8 : 4;
-    int mt = (int)((48 * 1024) / (2 * (size_t)n * esz));
+    int mt = (int)(budget / (2 * (size_t)n * esz));
     mt = std::max(8, mt / 8 * 8);
     mt = std::min(mt, (n + 7) / 8 * 8);
     if (mt % mb) mt = (mt / mb + 1) * mb;
@@ -355,7 +358,15 @@ int fp_tile_rows_ragged(int n, int prec, int mb)
 struct GroupCfg {
     int C = 0;
     int tpr = 0;
+    int ab_kib = 0;  // Fletcher-Powell: A/B tile budget in KiB (0: kAbDefaultKiB)
 };
+
+// The default budget of a Fletcher-Powell group's A/B tiles, and the large
+// one the tuner also tries: the uneven-batch kernel runs one CTA per SM (its
+// registers), so a larger tile costs no occupancy and halves or quarters the
+// tile loads and barriers of an evaluation at large n.
+constexpr int kAbDefaultKiB = 48;
+constexpr int kAbLargeKiB = 144;
 
 int n_bucket(int n)
 {
@@ -424,7 +435,8 @@ int build_plan(const chessfad_request *reqs, long long nreq, int prec, const Pla
         const long long np = (long long)g.second.size();
         const long long total_rows = np * n;
         const int maxpts = (int)std::min<long long>(np, (rows - 1) / n + 2);
-        const int mt = (fn == CHESSFAD_FLETCHER_POWELL) ? fp_tile_rows_ragged(n, prec, (C == 1) ? 8 : mb) : 8;
+        const size_t ab = (size_t)(gc.ab_kib ? gc.ab_kib : kAbDefaultKiB) * 1024;
+        const int mt = (fn == CHESSFAD_FLETCHER_POWELL) ? fp_tile_rows_ragged(n, prec, (C == 1) ? 8 : mb, ab) : 8;
         if (fn == CHESSFAD_FLETCHER_POWELL) pl->max_fp_n = std::max(pl->max_fp_n, n);
         const bool f64sweep = (prec == CHESSFAD_FP64) || n == 1;
         const size_t bytes = f64sweep ? smem_layout<double>(fn, true, n, maxpts, mt).total
@@ -436,7 +448,7 @@ int build_plan(const chessfad_request *reqs, long long nreq, int prec, const Pla
             const int stpr = sym_tpr(tpr, n);
             const int srows = kRaggedBlock / stpr;
             const int ntq = (n + srows - 1) / srows;
-            const int smt = fp_tile_rows_ragged(n, prec, mb);
+            const int smt = fp_tile_rows_ragged(n, prec, mb, ab);
             const size_t sbytes =
                 (prec == CHESSFAD_FP64)
                     ? align_up(smem_layout<double>(fn, true, n, 1, smt).total, 16) + sym_tile_extra<double>(n, C)
@@ -659,13 +671,15 @@ int chessfad_ragged_plan_info(chessfad_ragged_plan plan, size_t *workspace_bytes
     return CHESSFAD_SUCCESS;
 }
 
-int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, int fn, int n, int *csize, int *threads_per_row)
+int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, int fn, int n, int *csize, int *threads_per_row,
+                                      int *tile_rows)
 {
     if (!plan) return CHESSFAD_ERR_PLAN;
     for (const RTile &t : plan->tiles) {
         if (t.fn == fn && t.n == n) {
             if (csize) *csize = t.C;
             if (threads_per_row) *threads_per_row = t.tpr;
+            if (tile_rows) *tile_rows = t.mt;
             return CHESSFAD_SUCCESS;
         }
     }
@@ -740,6 +754,12 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
         int nmax = 0;
         for (const chessfad_request &r : sample) nmax = std::max(nmax, r.n);
         std::vector<GroupCfg> cands;
+        // A/B tile budgets that give different tile heights at this group's n
+        std::vector<int> abs{kAbDefaultKiB};
+        if (fn == CHESSFAD_FLETCHER_POWELL &&
+            fp_tile_rows_ragged(nmax, prec, 8, (size_t)kAbLargeKiB * 1024) !=
+                fp_tile_rows_ragged(nmax, prec, 8, (size_t)kAbDefaultKiB * 1024))
+            abs.push_back(kAbLargeKiB);
         for (int C : {16, 8}) {
             if (prec == CHESSFAD_FP32_COMP && nmax == 1 && C == 8) continue;  // n = 1 runs C = 1 either way
             const int nch = (nmax + C - 1) / C;
@@ -749,7 +769,7 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
                 const int eff = (fn == CHESSFAD_FLETCHER_POWELL && nmax >= kSymMinN) ? sym_tpr(tpr, nmax) : tpr;
                 if (std::find(seen.begin(), seen.end(), eff) != seen.end()) continue;
                 seen.push_back(eff);
-                cands.push_back(GroupCfg{C, eff});
+                for (int ab : abs) cands.push_back(GroupCfg{C, eff, ab});
             }
         }
         GroupCfg best;
@@ -805,7 +825,7 @@ int chessfad_ragged_autotune(const chessfad_request *reqs, long long nreq, int p
     return rc;
 }
 
-int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threads_per_row)
+int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threads_per_row, int *ab_kib)
 {
     if (prec != CHESSFAD_FP64 && prec != CHESSFAD_FP32_COMP) return CHESSFAD_ERR_PRECISION;
     if (fn < 0 || fn > 2) return CHESSFAD_ERR_FUNCTION;
@@ -815,6 +835,7 @@ int chessfad_ragged_tuned_config(int prec, int fn, int n, int *csize, int *threa
     if (it == g_tuned.end()) return CHESSFAD_ERR_CONFIG;
     if (csize) *csize = it->second.C;
     if (threads_per_row) *threads_per_row = it->second.tpr;
+    if (ab_kib) *ab_kib = it->second.ab_kib ? it->second.ab_kib : kAbDefaultKiB;
     return CHESSFAD_SUCCESS;
 }
 

@@ -182,10 +182,10 @@ def test_ragged_autotune_then_plan_parity():
         plan = cf.RaggedPlan(reqs, prec, 0)
         for f, n in ((R, 5), (A, 40), (F, 150), (F, 33)):
             tc = cf.chessfad_ragged_tuned_config(prec, f, n)
-            assert tc is not None and tc[0] in (8, 16) and 1 <= tc[1] <= 32
+            assert tc is not None and tc[0] in (8, 16) and 1 <= tc[1] <= 32 and tc[2] in (48, 144)
             if (f, n) in set(zip(rg.fns.tolist(), rg.ns.tolist())):
-                c, t = cf.chessfad_ragged_plan_group_config(plan.handle, f, n)
-                assert c == tc[0]
+                c, t, mt = cf.chessfad_ragged_plan_group_config(plan.handle, f, n)
+                assert c == tc[0] and mt >= 8
         d.out.fill_(float("nan"))
         plan.run(d.x, d.v, d.out, d.params)
         torch.cuda.synchronize()
