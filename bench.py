@@ -17,8 +17,11 @@ FP32 FFMA pipe).  ``achieved`` = FP instructions the kernel executes per launch
 (ncu thread-instruction counts, FMA = 2 flops, recorded in
 ``profiles/counts.json`` per point and keyed by a hash of the kernel sources;
 null when the sources changed since) / the launch's CUDA-event time;
-``peak`` = the library's FMA microbenchmark (``chessfad_peak_info``) measured in
-the same run on the same GPU.
+``peak`` = SMs x FMA lanes x 2 x the maximum SM clock (the unit-count figure);
+``peak_measured`` = the library's FMA microbenchmark (``chessfad_peak_info``)
+measured in the same run on the same GPU, reported beside it (in FP64 a stream
+of independent DFMAs sustains 84 % of the unit-count rate, and kernels with
+other instruction mixes exceed it, so it is not the ceiling).
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the launching stream, with a 256 MiB buffer written between steps to flush
@@ -194,12 +197,13 @@ def roofline_entry(counts: dict, key: str, units: int, ms: float, prec: int, pea
     return {
         "bound": "alu", "unit": "TFLOP/s", "kernel": kernel,
         "achieved": None if achieved is None else achieved / 1e12,
-        "peak": None if p["microbench"] is None else p["microbench"] / 1e12,
-        "frac": None if achieved is None or p["microbench"] is None else achieved / p["microbench"],
-        "peak_source": f"measured: chessfad_peak_info({PREC_NAME[prec]}) FMA microbenchmark in this run, "
-                       f"SM clock {p['microbench_sm_mhz'] and round(p['microbench_sm_mhz'])} MHz",
-        "peak_derived": None if p["derived"] is None else p["derived"] / 1e12,
-        "frac_of_derived": None if achieved is None or p["derived"] is None else achieved / p["derived"],
+        "peak": None if p["derived"] is None else p["derived"] / 1e12,
+        "frac": None if achieved is None or p["derived"] is None else achieved / p["derived"],
+        "peak_source": f"derived from unit counts and clock: {p['derived_note']}",
+        "peak_measured": None if p["microbench"] is None else p["microbench"] / 1e12,
+        "frac_of_measured": None if achieved is None or p["microbench"] is None else achieved / p["microbench"],
+        "peak_measured_source": f"chessfad_peak_info({PREC_NAME[prec]}) FMA microbenchmark in this run, "
+                                f"SM clock {p['microbench_sm_mhz'] and round(p['microbench_sm_mhz'])} MHz",
         "executed_flops_per_launch": executed,
         "model_flops_per_launch": model,
         "model_over_executed": None if executed is None else model / executed,
