@@ -1020,9 +1020,10 @@ def ingest_ncu(args):
            "command": args.ncu_command, "kernels": kernels}
     if keys["source_hash"] != kernel_source_hash():
         raise SystemExit("the kernel sources changed since the capture")
-    with open(COUNTS_FILE, "w") as f:
+    out_path = args.counts_out or COUNTS_FILE
+    with open(out_path, "w") as f:
         json.dump(doc, f, indent=1, sort_keys=True)
-    print(f"{len(kernels)} kernels -> {COUNTS_FILE}")
+    print(f"{len(kernels)} kernels -> {out_path}")
     # a markdown table of the capture (executed against model flops, DRAM
     # bytes against algorithmic bytes, per point)
     from paper_2410_22575_gb300 import workloads as W
@@ -1314,6 +1315,7 @@ def main():
                     help="where --profile-kernels writes, and --ingest-ncu reads, the launch order")
     ap.add_argument("--ingest-ncu", default=None, help="ncu CSV of --profile-kernels -> profiles/counts.json")
     ap.add_argument("--ncu-command", default="", help="the ncu command recorded in profiles/counts.json")
+    ap.add_argument("--counts-out", default=None, help="--ingest-ncu: output file (default profiles/counts.json)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--fn", type=int, default=None, help="kernel-only: function id instead of a named workload")
     ap.add_argument("--n", type=int, default=64)

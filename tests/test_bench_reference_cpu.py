@@ -9,9 +9,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "3", "--ref-budget", "4"], capture_output=True, text=True, timeout=600,
+    import time
+
+    t0 = time.perf_counter()
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "3", "--ref-budget", "6"], capture_output=True, text=True, timeout=600,
                        cwd=ROOT)
+    wall = time.perf_counter() - t0
     assert p.returncode == 0, p.stderr[-2000:]
     lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -23,3 +27,64 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+    # the same workload description as the GPU arm, and measured (not
+    # extrapolated) step times that fit inside the run
+    import bench
+
+    assert d["config"] == bench.headline_config(65536, 1)
+    assert d["dtype"] == "f64"
+    assert d["steps"] * d["ms_per_step"] * 1e-3 <= wall
+    assert abs(d["cpu_baseline"]["value"] - d["value"]) < 1e-9 * d["value"]
+
+
+def test_ingest_ncu_counts(tmp_path):
+    """--ingest-ncu turns an ncu CSV (one row per metric) into per-point
+    executed flops (2 x FMA + ADD + MUL) and DRAM bytes, matching launches to
+    the profile run's keys by kernel name."""
+    import json
+
+    import bench
+
+    keys = {"source_hash": bench.kernel_source_hash(), "launches": [
+        {"key": "ackley_n64/fp64/hvp/symmetric/c4", "batch": 100, "fn": 1, "prec": 0, "c": 4, "kind": "hvp",
+         "method": "symmetric", "config": {}},
+        {"key": "rosenbrock_n16/fp32_comp/hessian/plain/c8", "batch": 50, "fn": 0, "prec": 1, "c": 8,
+         "kind": "hessian", "method": "plain", "config": {}}]}
+    kp = tmp_path / "keys.json"
+    kp.write_text(json.dumps(keys))
+    hdr = ["ID", "Process ID", "Process Name", "Host Name", "Kernel Name", "Context", "Stream", "Block Size",
+           "Grid Size", "Device", "CC", "Section Name", "Metric Name", "Metric Unit", "Metric Value"]
+    rows = [hdr]
+    launches = [("void sym_kernel<double, double, 4, 1, 1, 8, 0>(SweepArgs)",
+                 {"smsp__sass_thread_inst_executed_op_dfma_pred_on.sum": "1,000", "dram__bytes_read.sum": "2000",
+                  "dram__bytes_write.sum": "0", "smsp__sass_thread_inst_executed_op_dadd_pred_on.sum": "10",
+                  "gpu__time_duration.sum": "5000"}),
+                ("void sweep_kernel<float, float, 8, 0, 0, 4>(SweepArgs)",
+                 {"smsp__sass_thread_inst_executed_op_ffma_pred_on.sum": "500",
+                  "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum": "5", "dram__bytes_read.sum": "100",
+                  "dram__bytes_write.sum": "50"})]
+    for i, (name, mets) in enumerate(launches):
+        for m, v in mets.items():
+            rows.append([str(i), "1", "python", "h", name, "1", "7", "(256, 1, 1)", "(10, 1, 1)", "0", "10.3",
+                         "Command line profiler metrics", m, "", v])
+    # an unrelated kernel between them is ignored
+    rows.insert(2, ["9", "1", "python", "h", "void fma_peak_kernel<double, 8>(int, double)", "1", "7", "", "", "0",
+                    "10.3", "x", "gpu__time_duration.sum", "ns", "1"])
+    cp = tmp_path / "counts.csv"
+    cp.write_text("==PROF== a header line\n" + "\n".join(",".join(f'"{c}"' for c in r) for r in rows) + "\n")
+    out = tmp_path / "counts.json"
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--ingest-ncu", str(cp), "--profile-keys",
+                        str(kp), "--counts-out", str(out)], capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    doc = json.loads(out.read_text())
+    assert doc["source_hash"] == bench.kernel_source_hash()
+    a = doc["kernels"]["ackley_n64/fp64/hvp/symmetric/c4"]
+    assert a["executed_flops_per_unit"] == (2 * 1000 + 10) / 100 and a["dram_bytes_per_unit"] == 20.0
+    r = doc["kernels"]["rosenbrock_n16/fp32_comp/hessian/plain/c8"]
+    assert r["executed_flops_per_unit"] == (2 * 500 + 5) / 50 and r["dram_bytes_per_unit"] == 3.0
+    # a launch that does not match its key is refused
+    keys["launches"][0]["c"] = 8
+    kp.write_text(json.dumps(keys))
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--ingest-ncu", str(cp), "--profile-keys",
+                        str(kp), "--counts-out", str(out)], capture_output=True, text=True, timeout=120, cwd=ROOT)
+    assert p.returncode != 0
