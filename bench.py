@@ -679,7 +679,7 @@ def ragged_arm(args, world, dev, stream, flush):
             "workspace_bytes": plan.info["workspace_bytes"], "plan_seconds": t_plan,
             "model_tflops": flops / (per * 1e-3) / 1e12,
             "_out": out.double().cpu().numpy(), "_x": x.double().cpu().numpy(), "_v": v.double().cpu().numpy(),
-            "_rg": rg, "_c": 16}
+            "_rg": rg, "_c": 16}  # the oracle's CHESS-VEC chunk size for the CPU baseline
 
 
 # ------------------------------------------------------------------ oracle leg
@@ -751,7 +751,6 @@ def ragged_cpu_baseline(r, t_closed_form_all, args):
     cap = args.ragged_cpu_cap
     cand = np.nonzero(cost <= cap)[0]
     order = rng.permutation(cand)
-    p = oracle.FPParams(rg.fp.A, rg.fp.B, rg.fp.E)
     cores = oracle.num_threads()
     budget = args.cpu_seconds
 

@@ -256,7 +256,9 @@ CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s);
  * kernel (sm_mhz may be NULL).  The FP32 shapes timed are 8 chains x 8 CTAs
  * and 16 chains x 4 CTAs of 256 threads per SM; FP64 adds 16 and 32 chains,
  * at 8 and 4 CTAs per SM; both also run with a multiplier and an addend per
- * chain instead of shared ones; the best is reported. */
+ * chain instead of shared ones, and as accumulation chains acc[l] = fma(s,
+ * v[l], acc[l]) (17 or 9 accumulators, one scalar per step); the best is
+ * reported. */
 CHESSFAD_API int chessfad_peak_info(int prec, double *flops_per_s, double *sm_mhz);
 
 /* ---------------------------------------------------------------------------

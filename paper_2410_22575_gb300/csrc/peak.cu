@@ -1,6 +1,8 @@
-// peak.cu -- CUDA-core FMA peak microbenchmark (the roofline denominator of
-// the ALU-bound sweep kernels).  Every thread runs NCH independent dependent
-// chains a = fma(a, m, b) over all SMs; one FMA counts as two flops.  The
+// peak.cu -- CUDA-core FMA peak microbenchmark (the measured counterpart of
+// the unit-count roofline of the ALU-bound sweep kernels).  Every thread runs
+// independent dependent FMA chains over all SMs, either through the
+// multiplicand (a = fma(a, m, b)) or through the addend (acc = fma(s, v,
+// acc)); one FMA counts as two flops.  The
 // result is folded into a never-taken store so the chains cannot be removed.
 // Several (chains per thread, CTAs per SM) shapes, with shared or per-chain
 // operands, are timed and the best is reported, so the number is the pipe's
@@ -96,15 +98,61 @@ __global__ void __launch_bounds__(256) fma_peak_kernel_ops(int iters, T seed)
     }
 }
 
+// Accumulation chains: acc[l] = fma(s, v[l], acc[l]) for l < L with one
+// scalar s per step (the shape of a scalar-times-hDual accumulation), the
+// dependency through the addend.  On GB300 the FP64 pipe sustains this shape
+// at its full rate, while chains through the multiplicand (the kernels
+// above) sustain about 84 % of it.
+template <typename T, int L>
+__global__ void __launch_bounds__(256) fma_peak_kernel_axpy(int iters, T seed)
+{
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long c0 = 0, t0 = 0;
+    if (timer) {
+        t0 = global_ns();
+        c0 = clock64();
+    }
+    T acc[L], v[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        acc[l] = T(0);
+        v[l] = seed + T(l) * T(1e-3) + T(threadIdx.x) * T(1e-7);
+    }
+    T s = T(1e-3) * T(threadIdx.x);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            s = fma(s, T(0.999999), T(1e-9));
+#pragma unroll
+            for (int l = 0; l < L; ++l) acc[l] = fma(s, v[l], acc[l]);
+        }
+    }
+    T r = T(0);
+#pragma unroll
+    for (int l = 0; l < L; ++l) r += acc[l];
+    if (r == T(-12345.0)) g_peak_sink<T> = r;
+    if (timer) {
+        const unsigned long long c1 = clock64();
+        const unsigned long long t1 = global_ns();
+        g_peak_clk[0] = c1 - c0;
+        g_peak_clk[1] = t1 - t0;
+    }
+}
+
 struct PeakResult {
     double flops = 0.0;
     double sm_mhz = 0.0;
 };
 
-template <typename T, int NCH, bool OPS = false>
+enum { kChains = 0, kChainsOps = 1, kAxpy = 2 };
+
+// NCH: chains per thread (kAxpy: L + 1 FMAs per step, L accumulators)
+template <typename T, int NCH, int KIND = kChains>
 static int measure(int iters, int blocks_per_sm, PeakResult *best)
 {
-    auto kern = OPS ? fma_peak_kernel_ops<T, NCH> : fma_peak_kernel<T, NCH>;
+    auto kern = KIND == kAxpy ? fma_peak_kernel_axpy<T, NCH>
+                              : (KIND == kChainsOps ? fma_peak_kernel_ops<T, NCH> : fma_peak_kernel<T, NCH>);
+    const int fmas_per_step = KIND == kAxpy ? NCH + 1 : NCH;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
@@ -132,7 +180,7 @@ static int measure(int iters, int blocks_per_sm, PeakResult *best)
             rc = CHESSFAD_ERR_CUDA;
             break;
         }
-        const double fl = 2.0 * NCH * 16.0 * (double)iters * (double)blocks * threads;
+        const double fl = 2.0 * fmas_per_step * 16.0 * (double)iters * (double)blocks * threads;
         const double f = fl / (ms * 1e-3);
         if (f > best->flops) {
             best->flops = f;
@@ -151,7 +199,8 @@ static int peak(int prec, PeakResult *r)
         // FP32: 128 lanes per SM; 8 chains at 8 CTAs of 256 per SM saturate.
         if ((rc = measure<float, 8>(40000, 8, r))) return rc;
         if ((rc = measure<float, 16>(20000, 4, r))) return rc;
-        return measure<float, 8, true>(40000, 8, r);
+        if ((rc = measure<float, 8, kChainsOps>(40000, 8, r))) return rc;
+        return measure<float, 17, kAxpy>(20000, 8, r);
     }
     if (prec == CHESSFAD_FP64) {
         // FP64: few lanes per SM and a long pipe: more chains per thread, and
@@ -160,8 +209,10 @@ static int peak(int prec, PeakResult *r)
         if ((rc = measure<double, 16>(400, 8, r))) return rc;
         if ((rc = measure<double, 16>(800, 4, r))) return rc;
         if ((rc = measure<double, 32>(400, 4, r))) return rc;
-        if ((rc = measure<double, 8, true>(800, 8, r))) return rc;
-        return measure<double, 16, true>(400, 4, r);
+        if ((rc = measure<double, 8, kChainsOps>(800, 8, r))) return rc;
+        if ((rc = measure<double, 16, kChainsOps>(400, 4, r))) return rc;
+        if ((rc = measure<double, 17, kAxpy>(400, 8, r))) return rc;
+        return measure<double, 9, kAxpy>(800, 8, r);
     }
     return CHESSFAD_ERR_PRECISION;
 }
