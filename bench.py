@@ -811,9 +811,18 @@ def cpu_baseline(b, c, args):
     t0 = time.perf_counter()
     oracle.hvp(b.fn, b.x[:m], b.v[:m])
     t_cf = time.perf_counter() - t0
-    return {"value": rate, "unit": "HVP/s", "cores": oracle.num_threads(), "kind": "oracle",
+    # one thread, as the paper's sequential CPU runs (Sec. VII)
+    cores = oracle.num_threads()
+    prev = oracle.set_num_threads(1)
+    try:
+        rate1, m1, dt1, _ = cpu_sample_time(b, c, max(1.0, args.cpu_seconds / 4))
+    finally:
+        oracle.set_num_threads(prev)
+    return {"value": rate, "unit": "HVP/s", "cores": cores, "kind": "oracle",
             "sample": f"first {m} of {b.batch} points, CHESS-VEC (Alg. 7) FP64 with c={c}, {dt:.1f} s",
-            "closed_form_hvp_per_s": m / t_cf}
+            "closed_form_hvp_per_s": m / t_cf,
+            "single_thread": {"value": rate1, "unit": "HVP/s", "cores": 1,
+                              "sample": f"first {m1} points, CHESS-VEC (Alg. 7) FP64 with c={c}, {dt1:.1f} s"}}
 
 
 def reference_arm(args):

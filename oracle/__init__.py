@@ -109,6 +109,8 @@ def _load():
             lib.orc_count_get.argtypes = [P, P]
             lib.orc_count_get.restype = None
             lib.orc_num_threads.restype = I
+            lib.orc_set_num_threads.argtypes = [I]
+            lib.orc_set_num_threads.restype = I
             _lib = lib
     return _lib
 
@@ -145,6 +147,12 @@ def _params(fn: int, params: FPParams | None):
 
 def num_threads() -> int:
     return _load().orc_num_threads()
+
+
+def set_num_threads(t: int) -> int:
+    """Threads of the OpenMP loops of later calls from this thread; returns
+    the previous setting."""
+    return _load().orc_set_num_threads(int(t))
 
 
 # ---------------------------------------------------------------- O1

@@ -932,3 +932,17 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads the OpenMP loops of the next calls use (from the calling thread);
+ * returns the previous setting. */
+int orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    const int old = omp_get_max_threads();
+    if (t > 0) omp_set_num_threads(t);
+    return old;
+#else
+    (void)t;
+    return 1;
+#endif
+}

@@ -472,3 +472,18 @@ def test_chunk_hess_call_counts(orc):
         cs = [2 ** e for e in range(0, 2 * k + 2)]
         cost = [1.5 * nn * (2 * nn + 2 * c + nn / c + 1) for c in cs]
         assert cs[int(np.argmin(cost))] == 2 ** k
+
+
+def test_oracle_thread_count_control(orc):
+    """set_num_threads (the bench's single-thread CPU figure) changes the
+    OpenMP thread count of later calls and returns the previous one; results
+    do not depend on it."""
+    b = W.make_batch(A, 12, 30, seed=3)
+    want = orc.chess_vec(A, b.x, b.v, 4)
+    prev = orc.set_num_threads(1)
+    try:
+        assert orc.num_threads() == 1
+        np.testing.assert_array_equal(orc.chess_vec(A, b.x, b.v, 4), want)
+    finally:
+        orc.set_num_threads(prev)
+    assert orc.num_threads() == prev
