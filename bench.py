@@ -694,7 +694,12 @@ def headline_error(res, prec):
     ref, hn = oracle.hvp(1, res["_x"], res["_v"], with_norm=True)
     e = metrics.hvp_errors(res["_out"], ref, hn, res["_v"])
     bound = metrics.FP64_BOUND if prec == 0 else metrics.FP32_COMP_BOUND
-    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound)}
+    # the spectral-norm normalisation as well (n <= 64), on the first 4096 points
+    k = min(4096, len(e))
+    es = metrics.hvp_errors_spectral(res["_out"][:k], ref[:k], oracle.hessian_batch(1, res["_x"][:k]),
+                                     res["_v"][:k])
+    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound),
+            "max_spectral": float(es.max()), "spectral_points": int(k)}
 
 
 def workload_error(row):
@@ -703,13 +708,18 @@ def workload_error(row):
 
     b = row["_b"]
     p = None if b.fp is None else oracle.FPParams(b.fp.A, b.fp.B, b.fp.E)
+    extra = {}
     if row["kind"] == "hvp":
         ref, hn = oracle.hvp(b.fn, row["_x"], row["_v"], p, with_norm=True)
         e = metrics.hvp_errors(row["_out"], ref, hn, row["_v"])
+        if b.n <= 64:
+            es = metrics.hvp_errors_spectral(row["_out"], ref, oracle.hessian_batch(b.fn, row["_x"], p), row["_v"])
+            extra = {"max_spectral": float(es.max())}
     else:
         e = metrics.hessian_errors(row["_out"], oracle.hessian_batch(b.fn, row["_x"], p))
     bound = metrics.FP64_BOUND if row["precision"] == "fp64" else metrics.FP32_COMP_BOUND
-    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound)}
+    return {**metrics.summary(e), "points": int(len(e)), "bound": bound, "within_bound": bool(e.max() <= bound),
+            **extra}
 
 
 def ragged_error_all(r):

@@ -6,7 +6,8 @@ Per point p (the normalisation the accuracy bounds are stated in):
 * Hessian:  e_p = ||H_p - H*_p||_F / (||H*_p||_F + 1e-300)
 
 Frobenius norms bound the spectral norm from above, so these errors are never
-smaller than the spectral-normalised ones by more than sqrt(n).
+smaller than the spectral-normalised ones by more than sqrt(n);
+hvp_errors_spectral gives the spectral-normalised HVP error.
 """
 from __future__ import annotations
 
@@ -23,6 +24,17 @@ def hvp_errors(r, r_ref, hnorm, v) -> np.ndarray:
     num = np.linalg.norm(r - r_ref, axis=-1)
     den = np.asarray(hnorm) * np.linalg.norm(v, axis=-1) + 1e-300
     return num / den
+
+
+def hvp_errors_spectral(r, r_ref, H_ref, v) -> np.ndarray:
+    """e_p = ||r_p - r*_p||_2 / (||H*_p||_2 ||v_p||_2): the spectral-norm
+    normalisation (never smaller than the Frobenius one)."""
+    r = np.asarray(r, dtype=np.float64)
+    r_ref = np.asarray(r_ref, dtype=np.float64)
+    v = np.asarray(v, dtype=np.float64)
+    num = np.linalg.norm(r - r_ref, axis=-1)
+    den = np.linalg.norm(np.asarray(H_ref, dtype=np.float64), ord=2, axis=(-2, -1)) * np.linalg.norm(v, axis=-1)
+    return num / (den + 1e-300)
 
 
 def hessian_errors(H, H_ref) -> np.ndarray:
