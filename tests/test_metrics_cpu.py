@@ -14,7 +14,9 @@ def test_hvp_error_normalisations():
     r = r_ref + np.array([[1e-6, 0.0]])
     e = metrics.hvp_errors(r, r_ref, np.array([5.0]), v)
     es = metrics.hvp_errors_spectral(r, r_ref, H, v)
-    assert abs(e[0] - 1e-6 / 5.0) < 1e-18 and abs(es[0] - 1e-6 / 4.0) < 1e-18
+    d = np.linalg.norm(r - r_ref)  # 1e-6 up to the rounding of r_ref + 1e-6
+    assert abs(d - 1e-6) < 1e-15
+    assert abs(e[0] - d / 5.0) < 1e-20 and abs(es[0] - d / 4.0) < 1e-20
     rng = np.random.Generator(np.random.PCG64(1))
     A = rng.normal(size=(20, 6, 6))
     H = A + A.transpose(0, 2, 1)
