@@ -143,10 +143,10 @@ typedef struct {
  * symmetric HVP stages a point's chunks on and above the diagonal chunks in
  * shared memory (about n (n + C) / 2 values per point) and sums whole rows,
  * reproducibly, for n up to about 280 (FP32) / 200 (FP64); beyond, it sums
- * each row in an FP64 shared-memory accumulator with atomic adds (the two
- * updates of Alg. 8), whose order varies, so FP64 results of such sizes can
- * differ from run to run in the last bits.  The symmetric Hessian writes
- * chunks and their mirror images directly, at any n. */
+ * each row in an FP64 shared-memory accumulator (the two updates of Alg. 8),
+ * adding each iteration's staged chunks in thread order, so results are
+ * bitwise reproducible at every n.  The symmetric Hessian writes chunks and
+ * their mirror images directly, at any n. */
 typedef struct {
     int csize;
     int threads_per_row;
@@ -434,7 +434,7 @@ CHESSFAD_API int chessfad_version(void);
  * SCHUNK-HESS, Alg. 6: threads_per_point threads share a point's (row, chunk
  * >= diagonal chunk) items; the HVP stages a point's chunks in shared memory,
  * or, where they do not fit, sums rows in FP64 shared-memory accumulators
- * with atomic adds, reproducible to the last FP64 bits only).  x, v, out, H
+ * fed in a fixed order, bitwise reproducible).  x, v, out, H
  * as for chessfad_hvp / chessfad_hessian, 1 <= n <= CHESSFAD_MAX_N.
  * --------------------------------------------------------------------------- */
 typedef struct chessfad_user_fn chessfad_user_fn;
