@@ -166,7 +166,10 @@ def test_user_symmetric_limits_and_config_errors():
     out = torch.empty_like(k.x)
     # the symmetric HVP's chunk matrix does not fit shared memory: FP64 row
     # accumulators instead, explicitly and by default
-    assert k.hvp_err(f.hvp(k.x, k.v, cfg=SYM)).max() <= 1e-12
+    first = f.hvp(k.x, k.v, cfg=SYM)
+    assert k.hvp_err(first).max() <= 1e-12
+    # the accumulators add each iteration's staged chunks in thread order
+    assert np.array_equal(first.cpu().numpy(), f.hvp(k.x, k.v, cfg=SYM).cpu().numpy())
     assert k.hvp_err(f.hvp(k.x, k.v)).max() <= 1e-12
     k32 = Case(W.MIX, 512, 3, 18, cf.FP32_COMP)
     assert k32.hvp_err(user_fn(W.MIX, 16, cf.FP32_COMP).hvp(k32.x, k32.v, cfg=SYM)).max() <= 1e-5
