@@ -315,7 +315,9 @@ CHESSFAD_API int chessfad_ragged_plan_group_config(chessfad_ragged_plan plan, in
  * requests (ranges as for chessfad_ragged_plan_create), run the persistent
  * kernel on a sample of the group's requests (in table order, enough rows to
  * fill the GPU about four times) for every chunk size (16, 8), lanes per
- * row (1 .. 32, the symmetric Fletcher-Powell tiles' effective values) and,
+ * row (1 .. 32; for the symmetric Fletcher-Powell tiles, whose (row, chunk)
+ * items are dealt to all 256 threads, this sets the rows per tile, 256 /
+ * lanes) and,
  * for Fletcher-Powell, shared-memory budget of the A/B row tiles (48 or 144
  * KiB, where they differ in tile height),
  * measuring the SM cycles its tiles take, summed over the CTAs (the group's

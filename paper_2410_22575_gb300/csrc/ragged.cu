@@ -18,10 +18,12 @@
 //
 // Fletcher-Powell requests with n >= kSymMinN (where nearly all of the cost
 // is) use the symmetric method, SC-HESS-VEC (Alg. 8): row i evaluates only
-// the chunks from its diagonal chunk on, about half the evaluations.  Each
-// off-diagonal-chunk entry H_ij serves r_i in the row's own sum and r_j, a
-// row usually in another tile.  A tile sums what its rows contribute to every
-// column in shared memory, in a fixed order (rows, then iterations), writes
+// the chunks from its diagonal chunk on, about half the evaluations.  A tile
+// holds rows of one request and deals their (row, chunk) items to its
+// threads round-robin.  Each off-diagonal-chunk entry H_ij serves r_i in the
+// row's own sum and r_j, a row usually in another tile.  A tile sums what its
+// items contribute to every column in shared memory, in a fixed order
+// (iterations, then threads), writes
 // that partial row vector to its own slot in the workspace, and the tile that
 // completes a request (a per-request tile counter) adds the request's slots
 // in tile order: the result does not depend on the order in which tiles run,
@@ -88,100 +90,104 @@ __host__ __device__ constexpr int ragged_mb(int C, bool f64) { return f64 ? (C <
 __host__ __device__ inline int sym_slot_base(int i0, int C) { return (i0 / C) * C; }
 
 // Shared memory a symmetric tile needs beyond the sweep's layout L: the
-// partial row vector (n doubles) and the per-iteration stage of the mirrored
-// entries (C values per thread).
+// partial row vector (n doubles) and the per-iteration stage of every
+// thread's item (SymStage: its chunk, its row dot, its row and chunk).
 template <typename T>
 __host__ __device__ inline size_t sym_tile_extra(int n, int C)
 {
-    return align_up((size_t)n * sizeof(double), 16) + (size_t)kRaggedBlock * C * sizeof(T);
+    const size_t stage = align_up((size_t)kRaggedBlock * C * sizeof(T), 16) +
+                         (size_t)kRaggedBlock * (sizeof(double) + 2 * sizeof(int));
+    return align_up((size_t)n * sizeof(double), 16) + stage;
+}
+
+// The (row, chunk) items of a symmetric tile: the rows i0 .. i0+nrows-1, row
+// i with the chunks from its diagonal chunk floor(i/C) on (SC-HESS-VEC,
+// Alg. 8), enumerated by chunk row R, then row, then chunk.
+__host__ __device__ inline int sym_tile_items(int i0, int nrows, int C, int nch)
+{
+    int items = 0;
+    for (int R = i0 / C; R * C < i0 + nrows; ++R) {
+        const int lo = R * C > i0 ? R * C : i0;
+        const int hi = (R + 1) * C < i0 + nrows ? (R + 1) * C : i0 + nrows;
+        items += (hi - lo) * (nch - R);
+    }
+    return items;
+}
+
+__device__ __forceinline__ void sym_tile_item(int k, int i0, int nrows, int C, int nch, int &i, int &cn)
+{
+    int R = i0 / C;
+    for (;; ++R) {
+        const int lo = R * C > i0 ? R * C : i0;
+        const int hi = (R + 1) * C < i0 + nrows ? (R + 1) * C : i0 + nrows;
+        const int cnt = (hi - lo) * (nch - R);
+        if (k < cnt || (R + 1) * C >= i0 + nrows) {
+            i = lo + k / (nch - R);
+            cn = R + k % (nch - R);
+            return;
+        }
+        k -= cnt;
+    }
 }
 
 // One symmetric tile: rows i0 .. i0+nrows-1 of one large Fletcher-Powell
-// request, tpr lanes per row; lane r of row i takes chunks c0 + r, c0 + r +
-// tpr, ... with c0 = floor(i/C) (SC-HESS-VEC, Alg. 8).  The trip count is the
-// tile's largest (the sweep's A/B tile loads are block-wide), lanes without a
-// chunk idle through the barriers.
+// request.  Its (row, chunk) items are dealt round-robin to the CTA's
+// threads, so every thread has an item in every iteration but the last
+// (rows with few chunks leave no lane idle).  Each iteration stages every
+// thread's chunk and row dot; after a barrier each column's owner adds, in
+// thread order, the row dots of its own row and the mirrored entries H_is v_i
+// of the chunks that hold its column (right of their row's diagonal chunk),
+// into the tile's FP64 partial row vector.  The trip count is the same for
+// every thread (the sweep's A/B tile loads are block-wide).
 template <typename T, int C, int MB>
 __device__ __forceinline__ void ragged_sym_tile(const RaggedArgs &a, const RTile &t, const Job &job,
                                                 const ListPoints &pm, unsigned char *smem)
 {
     __shared__ int s_last;
-    const int n = t.n, tpr = t.tpr;
+    const int n = t.n;
     const Smem<T> L = smem_layout<T>(FN_FP, true, n, t.maxpts, t.mt);
     double *part = reinterpret_cast<double *>(smem + align_up(L.total, 16));
-    T *stage = reinterpret_cast<T *>(smem + align_up(L.total, 16) + align_up((size_t)n * sizeof(double), 16));
+    const SymStage<T, C> stage(smem + align_up(L.total, 16) + align_up((size_t)n * sizeof(double), 16),
+                               (int)blockDim.x);
     const long long p = t.row0 / n;
     const int i0 = (int)(t.row0 - p * n);
     const int base = sym_slot_base(i0, C);
     const int tid = threadIdx.x;
     for (int e = tid; e < n - base; e += blockDim.x) part[e] = 0.0;
     point_prologue<T, T, FN_FP, true>(job, pm, smem, L, p, 1);  // ends with a barrier
-    const int r = tid % tpr;
-    const int ir = tid / tpr;
-    const bool active = ir < t.nrows;
-    const int i = active ? i0 + ir : i0;
     const PointTables<T> pt(smem, L, 0, n);
     const int q = a.list[t.list0 + p];
-    const int c0 = i / C;
-    const int iters = (t.nch - i0 / C + tpr - 1) / tpr;
-    using Dot = typename std::conditional<IsComp<T>::value, CSum, T>::type;
-    Dot own;
-    if constexpr (IsComp<T>::value) {
-        own.s = 0.f;
-        own.e = 0.f;
-    } else {
-        own = T(0);
-    }
+    const int items = sym_tile_items(i0, t.nrows, C, t.nch);
+    const int iters = (items + (int)blockDim.x - 1) / (int)blockDim.x;
     for (int it = 0; it < iters; ++it) {
-        const int j = c0 + r + it * tpr;
-        const bool has = active && j < t.nch;
-        const int cstart = j * C;
+        const int k = tid + it * (int)blockDim.x;
+        const bool has = k < items;
+        int i = i0, cn = i0 / C;
+        if (has) sym_tile_item(k, i0, t.nrows, C, t.nch, i, cn);
+        const int cstart = cn * C;
         const HD<T, C> f = row_chunk<T, C, FN_FP, MB, true>(job, smem, L, pt, i, cstart, has, it == 0);
+        double own = 0.0;  // products of two FP32 values are exact in FP64
         if (has) {
 #pragma unroll
-            for (int l = 0; l < C; ++l) {
-                if (cstart + l < n) {
-                    if constexpr (IsComp<T>::value) cdot_add(own, f.h[l], pt.v[cstart + l]);
-                    else own = fma_(f.h[l], pt.v[cstart + l], own);
-                }
-            }
+            for (int l = 0; l < C; ++l)
+                if (cstart + l < n) own = fma((double)f.h[l], (double)pt.v[cstart + l], own);
         }
-        // Mirror updates r_s += H_is v_i for the entries right of row i's
-        // diagonal chunk: stage every thread's chunk, then each column's owner
-        // adds them in row order.
-#pragma unroll
-        for (int l = 0; l < C; ++l) stage[l * kRaggedBlock + tid] = f.h[l];
+        stage.put(tid, f.h, own, has ? i : -1, cn);
         __syncthreads();
         for (int col = base + tid; col < n; col += blockDim.x) {
-            const int jc = col / C, l = col - jc * C;
+            const int ccn = col / C, cl = col - ccn * C;
             double sum = part[col - base];
-            for (int rr = 0; rr < t.nrows; ++rr) {
-                const int cc0 = (i0 + rr) / C;
-                const int lane = jc - cc0 - it * tpr;
-                if (jc > cc0 && lane >= 0 && lane < tpr)
-                    sum += (double)stage[l * kRaggedBlock + rr * tpr + lane] * (double)pt.v[i0 + rr];
+            for (int u = 0; u < (int)blockDim.x; ++u) {
+                const int ui = stage.row(u);
+                if (ui < 0) continue;
+                if (ui == col) sum += stage.own(u);
+                const int ucn = stage.chunk(u);
+                if (ucn == ccn && ucn > ui / C) sum += (double)stage.h(u, cl) * (double)pt.v[ui];
             }
             part[col - base] = sum;
         }
         __syncthreads();  // the stage is rewritten by the next iteration
     }
-    // the row's lanes (aligned groups inside one warp), then the row's own
-    // sum into its column of the tile's partial vector
-    double rowsum;
-    if constexpr (IsComp<T>::value) {
-        for (int off = tpr >> 1; off > 0; off >>= 1) {
-            CSum o;
-            o.s = __shfl_xor_sync(0xffffffffu, own.s, off);
-            o.e = __shfl_xor_sync(0xffffffffu, own.e, off);
-            own = csum_merge(own, o);
-        }
-        rowsum = (double)own.s + (double)own.e;
-    } else {
-        for (int off = tpr >> 1; off > 0; off >>= 1) own += __shfl_xor_sync(0xffffffffu, own, off);
-        rowsum = (double)own;
-    }
-    if (active && r == 0) part[i - base] += rowsum;
-    __syncthreads();
     // This tile's slot: after the slots of the request's earlier tiles.
     const int ti = i0 / t.srows;
     long long slot = a.soffs[q];
@@ -477,10 +483,9 @@ int build_plan(const chessfad_request *reqs, long long nreq, int prec, const Pla
                     t.nrows = std::min(srows, n - i0);
                     t.srows = srows;
                     t.ntiles_req = ntq;
-                    // the block runs the longest row's chunk count (the rows
-                    // starting at i0 have the most chunks)
-                    const int iters = (nch - i0 / C + stpr - 1) / stpr;
-                    const double cost = (double)iters * stpr * t.nrows * sweep + 2000.0;
+                    // the tile's (row, chunk) items, dealt to its threads
+                    const int iters = (sym_tile_items(i0, t.nrows, C, nch) + kRaggedBlock - 1) / kRaggedBlock;
+                    const double cost = (double)iters * kRaggedBlock * sweep + 2000.0;
                     work.push_back({cost, t});
                     pl->est_cost += cost;
                 }
