@@ -50,7 +50,7 @@ struct RTile {
     long long row0;     // first row of the tile in its group's row space
     long long npoints;  // points (requests) in the group
     int list0;          // group's first entry in the request list
-    int fn, n, C, nch, tpr, maxpts, mt;
+    int fn, n, C, nch, tpr, maxpts, mt;  // tpr: lanes per row (symmetric tiles: kRaggedBlock / rows)
     int sym;            // symmetric tile: rows row0 .. row0+nrows-1 of one point
     int nrows;
     int srows;          // symmetric: rows per tile of the request (the last tile may have fewer)
@@ -388,7 +388,8 @@ std::map<std::tuple<int, int, int>, GroupCfg> g_tuned;  // (prec, fn, bucket)
 // small, more lanes only when a row's chunks are many.
 int default_tpr(int nch) { return std::min(32, pow2_floor(std::max(1, nch / 8))); }
 
-// Symmetric tiles: rows of one point each; at least enough lanes per row that
+// Symmetric tiles: rows of one point each, kRaggedBlock / lanes of them (the
+// tile's items are dealt to all its threads); at least enough lanes per row that
 // a tile's rows do not outnumber the point's.
 int sym_tpr(int tpr, int n)
 {
