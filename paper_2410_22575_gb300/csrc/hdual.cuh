@@ -52,58 +52,74 @@ __device__ __forceinline__ HD<T, C> hzero()
     return r;
 }
 
+// The zero and the one of CHUNK-INIT's seeds.  Neither may be a constant the
+// compiler can fold: the seeds keep the dense semantics of the method, every
+// product with a seed zero or one is executed (as in a library whose seeds
+// are run-time values).  Where the values come from is a matter of the
+// pipe: on GB300 a DFMA that takes an operand from the zero register or from
+// the constant bank issues at about 83 % of the FP64 pipe's rate, one whose
+// operands are all general registers at 91-95 %, while FFMA runs faster with
+// constant operands (fewer register reads per issue slot).  So FP32 seeds use
+// an opaque move of 0 (the zero register) and a literal one, and FP64 seeds
+// read both from device memory, once per sweep.
+template <typename T>
+struct SeedK {
+    T z, one;
+};
+
+static __device__ __align__(16) double g_seed_zero_one[2] = {0.0, 1.0};
+
+template <typename T>
+__device__ __forceinline__ SeedK<T> seed_constants();
+template <>
+__device__ __forceinline__ SeedK<float> seed_constants<float>()
+{
+    SeedK<float> k;
+    asm volatile("mov.b32 %0, 0;" : "=f"(k.z));
+    k.one = 1.0f;
+    return k;
+}
+template <>
+__device__ __forceinline__ SeedK<double> seed_constants<double>()
+{
+    SeedK<double> k;
+    asm("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %2;\n\tld.global.nc.v2.f64 {%0, %1}, [ga];\n\t}"
+        : "=d"(k.z), "=d"(k.one)
+        : "l"(g_seed_zero_one));
+    return k;
+}
+
 // CHUNK-INIT (Alg. 4) for one variable k, generated on the fly instead of
 // materialising y[n]: <x_k, [k == i], e_{k - cstart} if k is in the chunk, 0>.
 template <typename T, int C>
-__device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart, T z)
+__device__ __forceinline__ HD<T, C> seed(T xk, int k, int i, int cstart, const SeedK<T> &s)
 {
     HD<T, C> y;
     y.v = xk;
-    y.d1 = (k == i) ? T(1) : z;
+    y.d1 = (k == i) ? s.one : s.z;
     const int d = k - cstart;
 #pragma unroll
     for (int l = 0; l < C; ++l) {
-        y.g[l] = (d == l) ? T(1) : z;
-        y.h[l] = z;
+        y.g[l] = (d == l) ? s.one : s.z;
+        y.h[l] = s.z;
     }
     return y;
 }
 
-// A zero the compiler cannot see through.  Seeds built from it keep the
-// dense semantics of the method: every product with a seed zero is executed
-// (as in a library whose seeds are runtime values), never folded away.
-template <typename T>
-__device__ __forceinline__ T opaque_zero();
-template <>
-__device__ __forceinline__ float opaque_zero<float>()
-{
-    float z;
-    asm volatile("mov.b32 %0, 0;" : "=f"(z));
-    return z;
-}
-template <>
-__device__ __forceinline__ double opaque_zero<double>()
-{
-    double z;
-    asm volatile("mov.b64 %0, 0;" : "=d"(z));
-    return z;
-}
-
 // CHUNK-INIT seeds with the chunk position known at compile time: variable
 // k with chunk offset P = k - cstart (P outside [0, C) for variables outside
-// the chunk).  With P a constant the seed needs no per-component selects; its
-// ones are literal (x * 1 is exact) and its zeros are the opaque zero z, so the
-// arithmetic that consumes the seed is the full dense rule.
+// the chunk).  With P a constant the seed needs no per-component selects, and
+// the arithmetic that consumes it is the full dense rule.
 template <typename T, int C, int P>
-__device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row, T z)
+__device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row, const SeedK<T> &s)
 {
     HD<T, C> y;
     y.v = xk;
-    y.d1 = is_row ? T(1) : z;
+    y.d1 = is_row ? s.one : s.z;
 #pragma unroll
     for (int l = 0; l < C; ++l) {
-        y.g[l] = (l == P) ? T(1) : z;
-        y.h[l] = z;
+        y.g[l] = (l == P) ? s.one : s.z;
+        y.h[l] = s.z;
     }
     return y;
 }

@@ -215,7 +215,7 @@ struct StaticFor {
 template <typename T, int C, int LIMIT, bool kRemap, bool kSparse = false, typename F>
 __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
-    const T z = opaque_zero<T>();
+    const SeedK<T> z = seed_constants<T>();
     const int lo = min(cstart, n), hi = min(cstart + C, n);
     auto chunk = [&]() {
         if constexpr (Unroll<C, LIMIT>::value) {
@@ -252,7 +252,7 @@ __device__ __forceinline__ void for_each_seed(const T *__restrict__ xs, int n, i
 template <typename T, int C, int LIMIT, bool kRemap, bool kSparse = false, typename F>
 __device__ __forceinline__ void for_each_pair(const T *__restrict__ xs, int n, int i, int cstart, F &&f)
 {
-    const T z = opaque_zero<T>();
+    const SeedK<T> z = seed_constants<T>();
     const int t0 = max(cstart - 1, 0);
     const int t1 = max(t0, min(cstart + C, n - 1));
     auto outside = [&](int k) {
@@ -322,7 +322,7 @@ template <typename T, int C, bool kRemap, bool kSparse>
 __device__ __forceinline__ HD<T, C> ackley_sweep(const AckEnt<T> *__restrict__ tab, const T *__restrict__ sc, int n,
                                                  int i, int cstart)
 {
-    const T z = opaque_zero<T>();
+    const SeedK<T> z = seed_constants<T>();
     HD<T, C> Sh = hzero<T, C>();  // S / 2: derivative components of sum y_k^2 / 2
     HD<T, C> Cs = hzero<T, C>();
     // y^2 / 2 by the unary rule (phi' = y, phi'' = 1), doubled once after the

@@ -84,7 +84,7 @@ __device__ __forceinline__ void user_sweep(const UserArgs &a)
     const int i = (int)(item - p * n);
     const T *xp = xs + (p - p0) * n;
     const T *vp = vs + (p - p0) * n;
-    const T z = opaque_zero<T>();
+    const SeedK<T> z = seed_constants<T>();
     const int nch = (n + C - 1) / C;
     RowDot<T> dot;
     for (int cn = 0; cn < nch; ++cn) {
@@ -133,7 +133,7 @@ __device__ __forceinline__ void user_sym(const UserArgs &a)
     const long long p = p0 + q;
     const T *xp = xs + (size_t)q * n;
     T *Hs = hs + (size_t)q * sym_hs_elems(n, C);
-    const T z = opaque_zero<T>();
+    const SeedK<T> z = seed_constants<T>();
     const int nch = (n + C - 1) / C;
     const int items = C * nch * (nch + 1) / 2;
     if (HVP && acc_form) {

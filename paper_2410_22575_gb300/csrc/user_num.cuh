@@ -211,7 +211,7 @@ template <typename T, int C>
 struct Vars {
     const T *x;
     int i, cstart;
-    T z;
+    SeedK<T> z;
     __device__ __forceinline__ Num<T, C> operator[](int k) const { return Num<T, C>(seed<T, C>(x[k], k, i, cstart, z)); }
 };
 
