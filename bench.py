@@ -123,20 +123,30 @@ def algorithmic_bytes(n: int, prec: int, kind: str) -> int:
 
 
 # Sources that define the batched sweep kernels: the executed-instruction
-# counts and DRAM traffic in profiles/counts.json are used only while these
-# are unchanged since the capture.
+# counts and DRAM traffic in profiles/counts.json are used only while the code
+# of these files (comments and whitespace aside) is unchanged since the capture.
 KERNEL_SOURCES = ("hdual.cuh", "sym_layout.cuh", "sweep.cuh", "dispatch.h", "point.cuh", "instances.cu")
 
 
-def kernel_source_hash() -> str:
+def code_tokens(text: str) -> str:
+    """C++/CUDA source without its comments, whitespace runs collapsed.  The
+    kernel sources hold no comment markers inside string literals."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
+def kernel_source_hash(csrc: str | None = None) -> str:
     import glob
 
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
+    csrc = csrc or os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
     for pat in KERNEL_SOURCES:
         for p in sorted(glob.glob(os.path.join(csrc, pat))):
             h.update(os.path.basename(p).encode())
-            h.update(open(p, "rb").read())
+            h.update(code_tokens(open(p, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -176,8 +186,15 @@ def device_peaks(cf, dev_index: int) -> dict:
         except Exception as e:  # report, do not hide
             print(f"peak microbenchmark failed: {e}", file=sys.stderr)
             f, mhz = None, None
+        try:
+            reg, lit = cf.chessfad_peak_operand_rates(prec)
+            operands = {"register": reg, "literal": lit, "literal_over_register": lit / reg}
+        except Exception as e:
+            print(f"operand microbenchmark failed: {e}", file=sys.stderr)
+            operands = None
         out[PREC_NAME[prec]] = {
             "microbench": f, "microbench_sm_mhz": mhz,
+            "axpy_operands": operands,
             "derived": None if max_mhz is None else sms * lanes * 2 * max_mhz * 1e6,
             "derived_note": f"{sms} SMs x {lanes} {'DFMA' if prec == 0 else 'FFMA'} lanes x 2 flop x "
                             f"{max_mhz} MHz (max SM clock)"}
@@ -1146,6 +1163,81 @@ def ragged_only(args):
                       "ms": ms, "hvp_per_s": len(sub.fns) / (min(ms) * 1e-3)}))
 
 
+def graph_timed(fn_call, reps: int) -> float:
+    """Device time per call in ms: reps calls captured in one CUDA graph and
+    replayed between two events (best of two replays), so host-side call
+    overhead (tens of microseconds through the binding) never leaves the GPU
+    idle inside the timed region -- it would dominate the small workloads."""
+    import torch
+
+    fn_call()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            fn_call()
+    g.replay()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        best = t if best is None else min(best, t)
+    return best
+
+
+def sparse_study(args):
+    """Seed-sparse symmetric method against the tuned dense method, every
+    named workload in both precisions: the dense rate is the HVP autotuner's
+    pick; the seed-sparse rate is the best over c in {4, 8, 16}, threads per
+    point in {32, 64, 128} and CTAs of 128 or 256 threads (kernel time, CUDA
+    graph replay).  The seed-sparse method skips variables whose seed has no
+    derivative part, which the paper's dense arithmetic does not."""
+    import torch
+
+    import paper_2410_22575_gb300 as cf
+    from paper_2410_22575_gb300 import workloads as W
+
+    rows = []
+    for name in ("rosenbrock_n16", "ackley_n64", "fletcher_powell_n32", "rosenbrock_n256"):
+        b = W.workload(name)
+        keep, params = [], None
+        if b.fn == W.FLETCHER_POWELL:
+            keep = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in (b.fp.A, b.fp.B, b.fp.E)]
+            params = cf.fp_params(*keep)
+        for prec, dt in ((cf.FP64, torch.float64), (cf.FP32_COMP, torch.float32)):
+            x = torch.tensor(b.x, dtype=dt, device="cuda")
+            v = torch.tensor(b.v, dtype=dt, device="cuda")
+            out = torch.empty_like(x)
+            reps = 5 if prec == cf.FP32_COMP else 2
+            cfg = cf.chessfad_autotune_hvp(b.fn, b.n, b.batch, x, v, out, params, prec)
+            t_dense = graph_timed(lambda: cf.chessfad_hvp(b.fn, b.n, b.batch, 0, x, v, out, params, prec), reps)
+            best = None
+            for c in (4, 8, 16):
+                for tpp in (32, 64, 128):
+                    for block in (128, 256):
+                        if block < tpp:
+                            continue
+                        sc = cf.Config(c, 0, block, cf.SYMMETRIC_SPARSE, tpp)
+                        t = graph_timed(lambda: cf.chessfad_hvp_config(b.fn, b.n, b.batch, sc, x, v, out, params,
+                                                                       prec), reps)
+                        if best is None or t < best[0]:
+                            best = (t, sc.as_dict())
+            row = {"workload": name, "precision": PREC_NAME[0 if prec == cf.FP64 else 1],
+                   "dense": {"config": cfg.as_dict(), "hvp_per_s": b.batch / (t_dense * 1e-3)},
+                   "seed_sparse": {"config": best[1], "hvp_per_s": b.batch / (best[0] * 1e-3)},
+                   "ratio": t_dense / best[0]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del x, v, out
+    return rows
+
+
 def report(args):
     """Per-workload table: HVP/s (and Hessians/s) for every
     named workload in both precisions, autotuned over both methods, plus the
@@ -1157,31 +1249,7 @@ def report(args):
 
     rows = []
     peaks = device_peaks(cf, 0)
-
-    def timed(fn_call, reps):
-        # device time per call: reps calls captured in one CUDA graph and
-        # replayed between two events, so host-side call overhead (tens of
-        # microseconds through the binding) never leaves the GPU idle inside
-        # the timed region -- it would dominate the small workloads
-        fn_call()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            for _ in range(reps):
-                fn_call()
-        g.replay()
-        torch.cuda.synchronize()
-        best = None
-        for _ in range(2):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            g.replay()
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / reps
-            best = t if best is None else min(best, t)
-        return best
+    timed = graph_timed
 
     for name in ("rosenbrock_n16", "ackley_n64", "fletcher_powell_n32", "rosenbrock_n256"):
         b = W.workload(name)
@@ -1326,6 +1394,7 @@ def main():
     ap.add_argument("--ragged-count", type=int, default=32)
     ap.add_argument("--report", action="store_true", help="per-workload table (all named workloads)")
     ap.add_argument("--chunk-study", action="store_true", help="measured best chunk size vs the Sec. V model")
+    ap.add_argument("--sparse-study", action="store_true", help="seed-sparse vs tuned dense method, every workload")
     ap.add_argument("--cpu-report", action="store_true", help="CPU-baseline leg for every named workload")
     ap.add_argument("--profile-kernels", action="store_true",
                     help="launch each kernel of the executed-count set once (the command ncu captures)")
@@ -1362,6 +1431,8 @@ def main():
         chunk_study(args)
     elif args.report:
         report(args)
+    elif args.sparse_study:
+        sparse_study(args)
     elif args.kernel_only:
         kernel_only(args)
     elif args.ragged_only:

@@ -261,6 +261,17 @@ CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s);
  * reported. */
 CHESSFAD_API int chessfad_peak_info(int prec, double *flops_per_s, double *sm_mhz);
 
+/* The accumulation-chain shape of chessfad_peak_info (17 accumulators,
+ * acc[l] = fma(s, v[l], acc[l])) timed twice: with the multipliers v[l] in
+ * general registers (*register_flops) and as literals, which the compiler
+ * turns into constant operands (*literal_flops).  It shows how the FMA pipe's
+ * rate depends on where one operand comes from: on GB300 the literal form
+ * runs at about 0.85 of the register form in FP64 and at the same rate in
+ * FP32.  Flop/s, one FMA = two flops.  Synchronises the device;
+ * allocates no device memory.  CHESSFAD_ERR_NULL for a NULL output,
+ * CHESSFAD_ERR_PRECISION for an unknown prec. */
+CHESSFAD_API int chessfad_peak_operand_rates(int prec, double *register_flops, double *literal_flops);
+
 /* ---------------------------------------------------------------------------
  * Uneven batches: requests of different functions and sizes in one launch.
  *

@@ -85,6 +85,8 @@ def load(build_if_missing: bool = True):
         lib.chessfad_autotune_hvp.argtypes = [I, I, L, P, P, P, P, I, P, P]
         lib.chessfad_peak_flops.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
         lib.chessfad_peak_info.argtypes = [I, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        lib.chessfad_peak_operand_rates.argtypes = [I, ctypes.POINTER(ctypes.c_double),
+                                                    ctypes.POINTER(ctypes.c_double)]
         lib.chessfad_kernel_info.argtypes = [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(L)]
         lib.chessfad_ragged_plan_create.argtypes = [P, L, I, I, ctypes.POINTER(P)]
         lib.chessfad_ragged_plan_destroy.argtypes = [P]
@@ -120,7 +122,7 @@ def load(build_if_missing: bool = True):
         for name in ("chessfad_hvp", "chessfad_hessian", "chessfad_hvp_config", "chessfad_hessian_config",
                      "chessfad_default_config", "chessfad_resolve_config", "chessfad_autotune_hvp",
                      "chessfad_autotune_hessian", "chessfad_peak_flops",
-                     "chessfad_peak_info",
+                     "chessfad_peak_info", "chessfad_peak_operand_rates",
                      "chessfad_kernel_info", "chessfad_version", "chessfad_ragged_plan_create",
                      "chessfad_ragged_plan_destroy", "chessfad_ragged_plan_info", "chessfad_ragged_plan_upload",
                      "chessfad_hvp_ragged", "chessfad_ragged_plan_group_config", "chessfad_ragged_autotune",
@@ -240,6 +242,16 @@ def chessfad_peak_info(prec) -> tuple[float, float]:
     mhz = ctypes.c_double()
     _check(load().chessfad_peak_info(prec, ctypes.byref(f), ctypes.byref(mhz)), "chessfad_peak_info")
     return f.value, mhz.value
+
+
+def chessfad_peak_operand_rates(prec) -> tuple[float, float]:
+    """(flop/s with register multipliers, flop/s with literal multipliers) of
+    the accumulation-chain FMA shape."""
+    r = ctypes.c_double()
+    lit = ctypes.c_double()
+    _check(load().chessfad_peak_operand_rates(prec, ctypes.byref(r), ctypes.byref(lit)),
+           "chessfad_peak_operand_rates")
+    return r.value, lit.value
 
 
 def chessfad_kernel_info(fn, prec, csize, hvp=True) -> dict:

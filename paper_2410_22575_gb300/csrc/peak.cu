@@ -100,10 +100,13 @@ __global__ void __launch_bounds__(256) fma_peak_kernel_ops(int iters, T seed)
 
 // Accumulation chains: acc[l] = fma(s, v[l], acc[l]) for l < L with one
 // scalar s per step (the shape of a scalar-times-hDual accumulation), the
-// dependency through the addend.  On GB300 the FP64 pipe sustains this shape
-// at its full rate, while chains through the multiplicand (the kernels
-// above) sustain about 84 % of it.
-template <typename T, int L>
+// dependency through the addend.  kLiteral: the v[l] are literals, so the
+// compiler takes them as constant operands (FP64: constant bank; FP32:
+// immediates) instead of general registers.  On GB300 the FP64 pipe sustains
+// the register form at 99 % of its nominal rate and the literal form, like
+// the chains above with their literal operands, at about 84 %; FFMA runs at
+// the same rate either way.
+template <typename T, int L, bool kLiteral = false>
 __global__ void __launch_bounds__(256) fma_peak_kernel_axpy(int iters, T seed)
 {
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(256) fma_peak_kernel_axpy(int iters, T seed)
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         acc[l] = T(0);
-        v[l] = seed + T(l) * T(1e-3) + T(threadIdx.x) * T(1e-7);
+        v[l] = kLiteral ? T(1) + T(l) * T(1e-3) : seed + T(l) * T(1e-3) + T(threadIdx.x) * T(1e-7);
     }
     T s = T(1e-3) * T(threadIdx.x);
     for (int it = 0; it < iters; ++it) {
@@ -144,15 +147,17 @@ struct PeakResult {
     double sm_mhz = 0.0;
 };
 
-enum { kChains = 0, kChainsOps = 1, kAxpy = 2 };
+enum { kChains = 0, kChainsOps = 1, kAxpy = 2, kAxpyLiteral = 3 };
 
 // NCH: chains per thread (kAxpy: L + 1 FMAs per step, L accumulators)
 template <typename T, int NCH, int KIND = kChains>
 static int measure(int iters, int blocks_per_sm, PeakResult *best)
 {
-    auto kern = KIND == kAxpy ? fma_peak_kernel_axpy<T, NCH>
-                              : (KIND == kChainsOps ? fma_peak_kernel_ops<T, NCH> : fma_peak_kernel<T, NCH>);
-    const int fmas_per_step = KIND == kAxpy ? NCH + 1 : NCH;
+    auto kern = KIND == kAxpy          ? fma_peak_kernel_axpy<T, NCH>
+                : KIND == kAxpyLiteral ? fma_peak_kernel_axpy<T, NCH, true>
+                : KIND == kChainsOps   ? fma_peak_kernel_ops<T, NCH>
+                                       : fma_peak_kernel<T, NCH>;
+    const int fmas_per_step = (KIND == kAxpy || KIND == kAxpyLiteral) ? NCH + 1 : NCH;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CHESSFAD_ERR_CUDA;
@@ -217,7 +222,35 @@ static int peak(int prec, PeakResult *r)
     return CHESSFAD_ERR_PRECISION;
 }
 
+// The accumulation-chain shape with its multipliers in general registers
+// and as literals, at the same shape (17 accumulators, 8 CTAs of 256 per SM
+// requested).
+static int operand_rates(int prec, PeakResult *reg, PeakResult *lit)
+{
+    if (prec == CHESSFAD_FP32_COMP) {
+        const int rc = measure<float, 17, kAxpy>(20000, 8, reg);
+        return rc ? rc : measure<float, 17, kAxpyLiteral>(20000, 8, lit);
+    }
+    if (prec == CHESSFAD_FP64) {
+        const int rc = measure<double, 17, kAxpy>(400, 8, reg);
+        return rc ? rc : measure<double, 17, kAxpyLiteral>(400, 8, lit);
+    }
+    return CHESSFAD_ERR_PRECISION;
+}
+
 }  // namespace chessfad
+
+extern "C" CHESSFAD_API int chessfad_peak_operand_rates(int prec, double *register_flops, double *literal_flops)
+{
+    if (!register_flops || !literal_flops) return CHESSFAD_ERR_NULL;
+    chessfad::PeakResult reg, lit;
+    const int rc = chessfad::operand_rates(prec, &reg, &lit);
+    if (rc == CHESSFAD_SUCCESS) {
+        *register_flops = reg.flops;
+        *literal_flops = lit.flops;
+    }
+    return rc;
+}
 
 extern "C" CHESSFAD_API int chessfad_peak_flops(int prec, double *flops_per_s)
 {

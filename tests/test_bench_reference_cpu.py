@@ -88,3 +88,23 @@ def test_ingest_ncu_counts(tmp_path):
     p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--ingest-ncu", str(cp), "--profile-keys",
                         str(kp), "--counts-out", str(out)], capture_output=True, text=True, timeout=120, cwd=ROOT)
     assert p.returncode != 0
+
+
+def test_kernel_source_hash_ignores_comments_only(tmp_path):
+    """The executed counts stay valid through comment and layout edits of the
+    kernel sources, and no longer through a change of their code."""
+    import shutil
+
+    import bench
+
+    csrc = os.path.join(ROOT, "paper_2410_22575_gb300", "csrc")
+    for pat in bench.KERNEL_SOURCES:
+        shutil.copy(os.path.join(csrc, pat), tmp_path / pat)
+    h0 = bench.kernel_source_hash(str(tmp_path))
+    assert h0 == bench.kernel_source_hash()
+    f = tmp_path / "hdual.cuh"
+    text = f.read_text()
+    f.write_text("// another comment\n" + text.replace("namespace chessfad {", "namespace chessfad  {  /* x */", 1))
+    assert bench.kernel_source_hash(str(tmp_path)) == h0
+    f.write_text(text.replace("T v, d1;", "T d1, v;", 1))
+    assert bench.kernel_source_hash(str(tmp_path)) != h0

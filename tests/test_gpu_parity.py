@@ -138,6 +138,9 @@ def test_kernel_info_and_peak():
     f64 = cf.chessfad_peak_flops(cf.FP64)
     assert 1e13 < f32 < 2e14
     assert 1e11 < f64 < f32
+    for prec in (cf.FP32_COMP, cf.FP64):
+        reg, lit = cf.chessfad_peak_operand_rates(prec)
+        assert 1e11 < reg < 2e14 and 1e11 < lit < 2e14
 
 
 # ------------------------------------------------------------------ symmetric method
