@@ -968,6 +968,9 @@ NCU_METRICS = ("gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.su
                "smsp__sass_thread_inst_executed_op_ffma_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_fadd_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_ffma2_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_fadd2_pred_on.sum,"
+               "smsp__sass_thread_inst_executed_op_fmul2_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_dfma_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_dadd_pred_on.sum,"
                "smsp__sass_thread_inst_executed_op_dmul_pred_on.sum")
@@ -1019,7 +1022,8 @@ def read_ncu_csv(path: str) -> list[dict]:
 def ingest_ncu(args):
     """profiles/counts.json from an ncu capture of --profile-kernels: per
     kernel key, executed FP flops per point (2 x FMA + ADD + MUL thread
-    instructions, FP32 and FP64) and DRAM bytes per point."""
+    instructions, FP32 and FP64; a packed FP32 instruction, FFMA2, FADD2 or
+    FMUL2, does two of them) and DRAM bytes per point."""
     keys = json.load(open(args.profile_keys))
     launches = [l for l in read_ncu_csv(args.ingest_ncu) if "sym_kernel" in l["name"] or "sweep_kernel" in l["name"]]
     if len(launches) != len(keys["launches"]):
@@ -1035,14 +1039,19 @@ def ingest_ncu(args):
                 int(targs[4]) != (1 if k["kind"] == "hvp" else 0):
             raise SystemExit(f"launch {nm} does not match {k['key']}")
         g = lambda m: l.get(f"smsp__sass_thread_inst_executed_op_{m}_pred_on.sum", 0.0)
-        fl = 2 * g("ffma") + g("fadd") + g("fmul") + 2 * g("dfma") + g("dadd") + g("dmul")
+        fp32 = 2 * g("ffma") + g("fadd") + g("fmul") + 2 * (2 * g("ffma2") + g("fadd2") + g("fmul2"))
+        fp64 = 2 * g("dfma") + g("dadd") + g("dmul")
+        fl = fp32 + fp64
         dram = l.get("dram__bytes_read.sum", float("nan")) + l.get("dram__bytes_write.sum", float("nan"))
         u = k["batch"]
         kernels[k["key"]] = {
             "kernel": nm, "config": k["config"], "points_captured": u,
             "executed_flops_per_unit": fl / u,
-            "fp32_flops_per_unit": (2 * g("ffma") + g("fadd") + g("fmul")) / u,
-            "fp64_flops_per_unit": (2 * g("dfma") + g("dadd") + g("dmul")) / u,
+            "fp32_flops_per_unit": fp32 / u,
+            "fp64_flops_per_unit": fp64 / u,
+            "fp32_packed_share": (2 * (g("ffma2") + g("fadd2") + g("fmul2")) /
+                                  (g("ffma") + g("fadd") + g("fmul") + 2 * (g("ffma2") + g("fadd2") + g("fmul2")))
+                                  if fp32 else 0.0),
             "dram_bytes_per_unit": None if math.isnan(dram) else dram / u,
             "duration_ns_captured": l.get("gpu__time_duration.sum"),
             "issue_active_pct": l.get("smsp__issue_active.avg.pct_of_peak_sustained_active"),
@@ -1050,7 +1059,8 @@ def ingest_ncu(args):
         }
     doc = {"source_hash": keys["source_hash"],
            "note": ("per point ('unit'): executed flops = 2 x FMA + ADD + MUL thread instructions (FP32 and "
-                    "FP64, predicated on), DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum, from one "
+                    "FP64, predicated on; a packed FP32 FFMA2 / FADD2 / FMUL2 counts twice), "
+                    "fp32_packed_share = share of the FP32 operations done by packed instructions, DRAM bytes = dram__bytes_read.sum + dram__bytes_write.sum, from one "
                     "ncu capture per kernel on a prefix of the workload (points_captured), divided by the points"),
            "command": args.ncu_command, "kernels": kernels}
     if keys["source_hash"] != kernel_source_hash():

@@ -125,6 +125,87 @@ __device__ __forceinline__ HD<T, C> seed_at(T xk, bool is_row, const SeedK<T> &s
     return y;
 }
 
+// ------------------------------------------------------------------ components
+// The derivative parts g[0..C) and h[0..C) are updated with one scalar factor
+// per step.  FP32 with an even C runs the pairs (l, l+1) as one packed
+// instruction (__ffma2_rn, __fmul2_rn, __fadd2_rn; sm_100 and later): each
+// component rounds exactly as the scalar __fmaf_rn, __fmul_rn or __fadd_rn,
+// in half the issued instructions (the FP32 sweeps are bound by instruction
+// issue).  The packed products and sums are never contracted into FMAs with
+// a later addition, so a user function's FP32 arithmetic follows its source
+// operation by operation.
+
+// acc[l] = fma(s, a[l], acc[l])
+template <typename T, int C>
+__device__ __forceinline__ void vfma(T s, const T (&a)[C], T (&acc)[C])
+{
+#pragma unroll
+    for (int l = 0; l < C; ++l) acc[l] = fma_(s, a[l], acc[l]);
+}
+template <int C>
+__device__ __forceinline__ void vfma(float s, const float (&a)[C], float (&acc)[C])
+{
+    if constexpr (C % 2 == 0) {
+        const float2 s2 = make_float2(s, s);
+#pragma unroll
+        for (int l = 0; l < C; l += 2) {
+            const float2 r = __ffma2_rn(s2, make_float2(a[l], a[l + 1]), make_float2(acc[l], acc[l + 1]));
+            acc[l] = r.x;
+            acc[l + 1] = r.y;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < C; ++l) acc[l] = __fmaf_rn(s, a[l], acc[l]);
+    }
+}
+
+// r[l] = s * a[l]
+template <typename T, int C>
+__device__ __forceinline__ void vmul(T s, const T (&a)[C], T (&r)[C])
+{
+#pragma unroll
+    for (int l = 0; l < C; ++l) r[l] = s * a[l];
+}
+template <int C>
+__device__ __forceinline__ void vmul(float s, const float (&a)[C], float (&r)[C])
+{
+    if constexpr (C % 2 == 0) {
+        const float2 s2 = make_float2(s, s);
+#pragma unroll
+        for (int l = 0; l < C; l += 2) {
+            const float2 p = __fmul2_rn(s2, make_float2(a[l], a[l + 1]));
+            r[l] = p.x;
+            r[l + 1] = p.y;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < C; ++l) r[l] = s * a[l];
+    }
+}
+
+// r[l] = a[l] + b[l]
+template <typename T, int C>
+__device__ __forceinline__ void vadd(const T (&a)[C], const T (&b)[C], T (&r)[C])
+{
+#pragma unroll
+    for (int l = 0; l < C; ++l) r[l] = a[l] + b[l];
+}
+template <int C>
+__device__ __forceinline__ void vadd(const float (&a)[C], const float (&b)[C], float (&r)[C])
+{
+    if constexpr (C % 2 == 0) {
+#pragma unroll
+        for (int l = 0; l < C; l += 2) {
+            const float2 t = __fadd2_rn(make_float2(a[l], a[l + 1]), make_float2(b[l], b[l + 1]));
+            r[l] = t.x;
+            r[l + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < C; ++l) r[l] = a[l] + b[l];
+    }
+}
+
 // u * w (Fig. 1).
 template <typename T, int C>
 __device__ __forceinline__ HD<T, C> hmul(const HD<T, C> &a, const HD<T, C> &b)
@@ -132,11 +213,12 @@ __device__ __forceinline__ HD<T, C> hmul(const HD<T, C> &a, const HD<T, C> &b)
     HD<T, C> r;
     r.v = a.v * b.v;
     r.d1 = fma_(b.v, a.d1, a.v * b.d1);
-#pragma unroll
-    for (int l = 0; l < C; ++l) r.g[l] = fma_(b.v, a.g[l], a.v * b.g[l]);
-#pragma unroll
-    for (int l = 0; l < C; ++l)
-        r.h[l] = fma_(b.v, a.h[l], fma_(b.d1, a.g[l], fma_(a.d1, b.g[l], a.v * b.h[l])));
+    vmul(a.v, b.g, r.g);
+    vfma(b.v, a.g, r.g);
+    vmul(a.v, b.h, r.h);
+    vfma(a.d1, b.g, r.h);
+    vfma(b.d1, a.g, r.h);
+    vfma(b.v, a.h, r.h);
     return r;
 }
 
@@ -144,14 +226,15 @@ __device__ __forceinline__ HD<T, C> hmul(const HD<T, C> &a, const HD<T, C> &b)
 template <typename T, int C>
 __device__ __forceinline__ HD<T, C> hfma(const HD<T, C> &a, const HD<T, C> &b, const HD<T, C> &acc)
 {
-    HD<T, C> r;
+    HD<T, C> r = acc;
     r.v = fma_(a.v, b.v, acc.v);
     r.d1 = fma_(b.v, a.d1, fma_(a.v, b.d1, acc.d1));
-#pragma unroll
-    for (int l = 0; l < C; ++l) r.g[l] = fma_(b.v, a.g[l], fma_(a.v, b.g[l], acc.g[l]));
-#pragma unroll
-    for (int l = 0; l < C; ++l)
-        r.h[l] = fma_(b.v, a.h[l], fma_(b.d1, a.g[l], fma_(a.d1, b.g[l], fma_(a.v, b.h[l], acc.h[l]))));
+    vfma(a.v, b.g, r.g);
+    vfma(b.v, a.g, r.g);
+    vfma(a.v, b.h, r.h);
+    vfma(a.d1, b.g, r.h);
+    vfma(b.d1, a.g, r.h);
+    vfma(b.v, a.h, r.h);
     return r;
 }
 
@@ -161,11 +244,8 @@ __device__ __forceinline__ HD<T, C> hadd(const HD<T, C> &a, const HD<T, C> &b)
     HD<T, C> r;
     r.v = a.v + b.v;
     r.d1 = a.d1 + b.d1;
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        r.g[l] = a.g[l] + b.g[l];
-        r.h[l] = a.h[l] + b.h[l];
-    }
+    vadd(a.g, b.g, r.g);
+    vadd(a.h, b.h, r.h);
     return r;
 }
 
@@ -190,11 +270,8 @@ __device__ __forceinline__ HD<T, C> smul(T s, const HD<T, C> &a)
     HD<T, C> r;
     r.v = s * a.v;
     r.d1 = s * a.d1;
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        r.g[l] = s * a.g[l];
-        r.h[l] = s * a.h[l];
-    }
+    vmul(s, a.g, r.g);
+    vmul(s, a.h, r.h);
     return r;
 }
 
@@ -221,11 +298,9 @@ __device__ __forceinline__ HD<T, C> unary(const HD<T, C> &a, T phi, T dphi, T d2
     r.v = phi;
     r.d1 = dphi * a.d1;
     const T q = d2phi * a.d1;
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        r.g[l] = dphi * a.g[l];
-        r.h[l] = fma_(q, a.g[l], dphi * a.h[l]);
-    }
+    vmul(dphi, a.g, r.g);
+    vmul(dphi, a.h, r.h);
+    vfma(q, a.g, r.h);
     return r;
 }
 
@@ -238,11 +313,9 @@ __device__ __forceinline__ void sfma_unary(HD<T, C> &acc, T s, const HD<T, C> &a
     const T sd = s * dphi;
     const T q = (s * d2phi) * a.d1;
     acc.d1 = fma_(sd, a.d1, acc.d1);
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        acc.g[l] = fma_(sd, a.g[l], acc.g[l]);
-        acc.h[l] = fma_(sd, a.h[l], fma_(q, a.g[l], acc.h[l]));
-    }
+    vfma(sd, a.g, acc.g);
+    vfma(q, a.g, acc.h);
+    vfma(sd, a.h, acc.h);
 }
 
 // acc + s * u, componentwise; the value component only when kValue.
@@ -251,11 +324,8 @@ __device__ __forceinline__ void sfma(HD<T, C> &acc, T s, const HD<T, C> &a)
 {
     if (kValue) acc.v = fma_(s, a.v, acc.v);
     acc.d1 = fma_(s, a.d1, acc.d1);
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        acc.g[l] = fma_(s, a.g[l], acc.g[l]);
-        acc.h[l] = fma_(s, a.h[l], acc.h[l]);
-    }
+    vfma(s, a.g, acc.g);
+    vfma(s, a.h, acc.h);
 }
 
 // acc + phi(u) (s = 1 of the above).
@@ -265,11 +335,9 @@ __device__ __forceinline__ void add_unary(HD<T, C> &acc, const HD<T, C> &a, T ph
     if (kValue) acc.v += phi;
     const T q = d2phi * a.d1;
     acc.d1 = fma_(dphi, a.d1, acc.d1);
-#pragma unroll
-    for (int l = 0; l < C; ++l) {
-        acc.g[l] = fma_(dphi, a.g[l], acc.g[l]);
-        acc.h[l] = fma_(dphi, a.h[l], fma_(q, a.g[l], acc.h[l]));
-    }
+    vfma(dphi, a.g, acc.g);
+    vfma(q, a.g, acc.h);
+    vfma(dphi, a.h, acc.h);
 }
 
 // ---------------------------------------------------------------------------

@@ -39,8 +39,8 @@ def test_reference_arm_json_line():
 
 def test_ingest_ncu_counts(tmp_path):
     """--ingest-ncu turns an ncu CSV (one row per metric) into per-point
-    executed flops (2 x FMA + ADD + MUL) and DRAM bytes, matching launches to
-    the profile run's keys by kernel name."""
+    executed flops (2 x FMA + ADD + MUL, packed FP32 instructions twice) and
+    DRAM bytes, matching launches to the profile run's keys by kernel name."""
     import json
 
     import bench
@@ -61,7 +61,10 @@ def test_ingest_ncu_counts(tmp_path):
                   "gpu__time_duration.sum": "5000"}),
                 ("void sweep_kernel<float, float, 8, 0, 0, 4>(SweepArgs)",
                  {"smsp__sass_thread_inst_executed_op_ffma_pred_on.sum": "500",
-                  "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum": "5", "dram__bytes_read.sum": "100",
+                  "smsp__sass_thread_inst_executed_op_fmul_pred_on.sum": "5",
+                  "smsp__sass_thread_inst_executed_op_ffma2_pred_on.sum": "200",
+                  "smsp__sass_thread_inst_executed_op_fmul2_pred_on.sum": "3",
+                  "smsp__sass_thread_inst_executed_op_fadd2_pred_on.sum": "1", "dram__bytes_read.sum": "100",
                   "dram__bytes_write.sum": "50"})]
     for i, (name, mets) in enumerate(launches):
         for m, v in mets.items():
@@ -81,7 +84,10 @@ def test_ingest_ncu_counts(tmp_path):
     a = doc["kernels"]["ackley_n64/fp64/hvp/symmetric/c4"]
     assert a["executed_flops_per_unit"] == (2 * 1000 + 10) / 100 and a["dram_bytes_per_unit"] == 20.0
     r = doc["kernels"]["rosenbrock_n16/fp32_comp/hessian/plain/c8"]
-    assert r["executed_flops_per_unit"] == (2 * 500 + 5) / 50 and r["dram_bytes_per_unit"] == 3.0
+    # a packed FP32 instruction does two operations: FFMA2 = 4 flops, FMUL2 and FADD2 = 2
+    assert r["executed_flops_per_unit"] == (2 * 500 + 5 + 4 * 200 + 2 * 3 + 2 * 1) / 50
+    assert r["dram_bytes_per_unit"] == 3.0
+    assert r["fp32_packed_share"] == 2 * (200 + 3 + 1) / (500 + 5 + 2 * (200 + 3 + 1))
     # a launch that does not match its key is refused
     keys["launches"][0]["c"] = 8
     kp.write_text(json.dumps(keys))
