@@ -14,14 +14,13 @@ n=32) in both precisions, ``ragged_100k`` the 100000-request uneven batch.
 
 Roofline: the sweep kernels are bound by CUDA-core arithmetic (FP64 DFMA or
 FP32 FFMA pipe).  ``achieved`` = FP instructions the kernel executes per launch
-(ncu thread-instruction counts, FMA = 2 flops, recorded in
-``profiles/counts.json`` per point and keyed by a hash of the kernel sources;
-null when the sources changed since) / the launch's CUDA-event time;
-``peak`` = SMs x FMA lanes x 2 x the maximum SM clock (the unit-count figure);
-``peak_measured`` = the library's FMA microbenchmark (``chessfad_peak_info``)
-measured in the same run on the same GPU, reported beside it (in FP64 a stream
-of independent DFMAs sustains 84 % of the unit-count rate, and kernels with
-other instruction mixes exceed it, so it is not the ceiling).
+(ncu thread-instruction counts, FMA = 2 flops, a packed FP32 instruction
+twice, recorded in ``profiles/counts.json`` per point and keyed by a hash of
+the kernel sources' code; null when that code changed since) / the launch's
+CUDA-event time; ``peak`` = SMs x FMA lanes x 2 x the maximum SM clock (the
+unit-count figure); ``peak_measured`` = the library's FMA microbenchmark
+(``chessfad_peak_info``, the best of several chain shapes) measured in the
+same run on the same GPU, reported beside it.
 
 Timing: W untimed warm-up steps, then K steps each bracketed by CUDA events
 on the launching stream, with a 256 MiB buffer written between steps to flush
