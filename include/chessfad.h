@@ -273,6 +273,44 @@ CHESSFAD_API int chessfad_peak_info(int prec, double *flops_per_s, double *sm_mh
 CHESSFAD_API int chessfad_peak_operand_rates(int prec, double *register_flops, double *literal_flops);
 
 /* ---------------------------------------------------------------------------
+ * Compensated-FP32 primitives.  The paper computes in FP64 (Sec. IV); the
+ * CHESSFAD_FP32_COMP precision rests on error-free transformations and
+ * compensated sums from the literature, and these two calls run the very
+ * device routines the sweep kernels use over caller arrays, so that their
+ * defining properties can be checked directly.  All pointers device, float,
+ * caller-owned; stream-ordered; no allocation, no host synchronisation.
+ * ------------------------------------------------------------------------- */
+
+/* Elementwise over k < count:
+ *   TwoSum (Knuth, TAOCP vol. 2):  s[k] = fl(a[k] + b[k]) and e[k] with
+ *                                  s[k] + e[k] == a[k] + b[k] exactly;
+ *   TwoProd (by FMA):              p[k] = fl(a[k] * b[k]) and q[k] =
+ *                                  fma(a[k], b[k], -p[k]), so p[k] + q[k] ==
+ *                                  a[k] * b[k] exactly unless q underflows.
+ * Any of s, e, p, q may be NULL (that output is skipped).  count == 0 is a
+ * no-op; CHESSFAD_ERR_BATCH for count < 0, CHESSFAD_ERR_NULL for a NULL a
+ * or b. */
+CHESSFAD_API int chessfad_eft(const float *a, const float *b, long long count, float *s, float *e, float *p,
+                              float *q, chessfad_stream_t stream);
+
+/* Compensated sums of the rows of a ([rows][len], row-major): Dot2 of a's
+ * and b's rows (b != NULL) or Sum2 of a's rows (b == NULL), both from Ogita,
+ * Rump & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
+ * 2005 (each rounding error, found by TwoSum and TwoProd, is added into a
+ * second accumulator, and the two are added once at the end), in the order
+ * of the compensated-FP32 row-times-v reduction of the HVP kernels: `lanes`
+ * (1, 2, 4, 8, 16 or 32) lanes per row, lane r taking the blocks r, r +
+ * lanes, r + 2 lanes, ... of `chunk` consecutive elements in ascending
+ * order, then the lanes merged pairwise at distances lanes/2, ..., 1 (the
+ * lanes' sums added by TwoSum, their error terms added plainly).  out[r]
+ * receives row r's result (rows floats).  rows == 0 is a no-op; len == 0
+ * gives zeros.  CHESSFAD_ERR_BATCH for rows < 0, len < 0 or rows * len
+ * beyond 64 bits, CHESSFAD_ERR_CONFIG for a bad lanes or chunk < 1,
+ * CHESSFAD_ERR_NULL for a NULL out (or a NULL a with len > 0). */
+CHESSFAD_API int chessfad_compensated_rows(const float *a, const float *b, long long rows, int len, int lanes,
+                                           int chunk, float *out, chessfad_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * Uneven batches: requests of different functions and sizes in one launch.
  *
  * Request q evaluates out[off .. off+n) = H_fn(x[off .. off+n)) v[off .. off+n)

@@ -88,6 +88,10 @@ def load(build_if_missing: bool = True):
         lib.chessfad_peak_operand_rates.argtypes = [I, ctypes.POINTER(ctypes.c_double),
                                                     ctypes.POINTER(ctypes.c_double)]
         lib.chessfad_kernel_info.argtypes = [I, I, I, I, ctypes.POINTER(I), ctypes.POINTER(L)]
+        lib.chessfad_eft.argtypes = [P, P, L, P, P, P, P, P]
+        lib.chessfad_eft.restype = I
+        lib.chessfad_compensated_rows.argtypes = [P, P, L, I, I, I, P, P]
+        lib.chessfad_compensated_rows.restype = I
         lib.chessfad_ragged_plan_create.argtypes = [P, L, I, I, ctypes.POINTER(P)]
         lib.chessfad_ragged_plan_destroy.argtypes = [P]
         lib.chessfad_ragged_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(L),
@@ -252,6 +256,19 @@ def chessfad_peak_operand_rates(prec) -> tuple[float, float]:
     _check(load().chessfad_peak_operand_rates(prec, ctypes.byref(r), ctypes.byref(lit)),
            "chessfad_peak_operand_rates")
     return r.value, lit.value
+
+
+def chessfad_eft(a, b, count, s=None, e=None, p=None, q=None, stream=None) -> int:
+    """TwoSum (s, e) and TwoProd (p, q) of float device arrays a, b, elementwise;
+    returns the status."""
+    return load().chessfad_eft(_addr(a), _addr(b), count, _addr(s), _addr(e), _addr(p), _addr(q), _stream(stream))
+
+
+def chessfad_compensated_rows(a, b, rows, length, lanes, chunk, out, stream=None) -> int:
+    """Dot2 of the rows of a and b (Sum2 of a's rows when b is None) in the
+    lane order of the compensated-FP32 row reduction; returns the status."""
+    return load().chessfad_compensated_rows(_addr(a), _addr(b), rows, length, lanes, chunk, _addr(out),
+                                            _stream(stream))
 
 
 def chessfad_kernel_info(fn, prec, csize, hvp=True) -> dict:

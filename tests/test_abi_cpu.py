@@ -92,6 +92,26 @@ def test_host_pipeline_argument_errors_without_gpu():
     assert lib.chessfad_hvp_host(0, 8, 0, 4, None, None, None, None, None, None, None, 0, 0, None) == 0
 
 
+def test_compensated_primitives_argument_errors_without_gpu():
+    # every rejection happens on the host, before a launch (no device pointer
+    # is ever dereferenced: the calls below launch nothing)
+    lib = cf.load()
+    d = ctypes.c_void_p(16)
+    assert lib.chessfad_eft(d, d, -1, d, d, d, d, None) == -3
+    assert lib.chessfad_eft(None, d, 8, d, d, d, d, None) == -5
+    assert lib.chessfad_eft(d, None, 8, d, d, d, d, None) == -5
+    assert lib.chessfad_eft(None, None, 0, None, None, None, None, None) == 0
+    assert lib.chessfad_compensated_rows(d, d, -1, 8, 4, 1, d, None) == -3
+    assert lib.chessfad_compensated_rows(d, d, 4, -1, 4, 1, d, None) == -3
+    assert lib.chessfad_compensated_rows(d, d, 2**62, 8, 4, 1, d, None) == -3
+    for lanes in (0, 3, 6, 64):
+        assert lib.chessfad_compensated_rows(d, d, 4, 8, lanes, 1, d, None) == -9
+    assert lib.chessfad_compensated_rows(d, d, 4, 8, 4, 0, d, None) == -9
+    assert lib.chessfad_compensated_rows(d, d, 4, 8, 4, 1, None, None) == -5
+    assert lib.chessfad_compensated_rows(None, d, 4, 8, 4, 1, d, None) == -5
+    assert lib.chessfad_compensated_rows(None, None, 0, 8, 4, 1, None, None) == 0
+
+
 def test_untuned_default_is_symmetric_at_the_sec5_chunk():
     """Untuned default: the symmetric method for n >= 4 with csize near the
     Sec. V optimum sqrt(n/2) (a power of two at or above it, capped by the
