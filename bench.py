@@ -606,7 +606,48 @@ def gpu_arm(args):
             e, t_all = ragged_error_all(ragged)
             line["ragged_100k"]["error_vs_oracle"] = e
             line["ragged_100k"]["cpu_baseline"] = ragged_cpu_baseline(ragged, t_all, args)
+    try:
+        line["summary"] = compact_summary(line)
+    except Exception as exc:  # the summary repeats figures; it must never cost the line
+        line["summary"] = {"error": repr(exc)}
     print(json.dumps(line))
+
+
+def _sig(x, digits: int = 3):
+    return None if x is None else float(f"{x:.{digits}g}")
+
+
+def compact_summary(line: dict) -> dict:
+    """The line's figures in a few hundred characters, printed as its last
+    key so that the end of the output carries every workload's numbers:
+    per entry [rate, roofline frac (executed flops / unit-count peak), e2e
+    rate or null, max error against the oracle or null]."""
+    def err(d):
+        return _sig((d.get("error_vs_oracle") or {}).get("max"), 2)
+
+    def frac(d):
+        return _sig((d.get("roofline") or {}).get("frac"))
+
+    out = {"fields": "rate, frac, e2e rate, max err",
+           "fp64": [_sig(line["value"], 4), frac(line), _sig(line["e2e"]["value"], 4), err(line)]}
+    f32 = line.get("fp32_comp")
+    if f32:
+        out["fp32_comp"] = [_sig(f32["value"], 4), frac(f32), _sig(f32["e2e"]["value"], 4), err(f32)]
+    for k, r in (line.get("workloads") or {}).items():
+        rate = r.get("hvp_per_s", r.get("hessians_per_s"))
+        out[k] = [_sig(rate), frac(r), None, err(r)]
+    rg = line.get("ragged_100k")
+    if rg:
+        untuned = rg.get("untuned_ms_per_step")
+        out["ragged_100k"] = {"s_per_step": _sig(rg["ms_per_step"] / 1e3), "hvp_per_s": _sig(rg["value"]),
+                              "untuned_s": None if untuned is None else _sig(untuned / 1e3),
+                              "max_err": err(rg),
+                              "requests_checked": (rg.get("error_vs_oracle") or {}).get("requests"),
+                              "cpu_hvp_per_s": _sig((rg.get("cpu_baseline") or {}).get("value"))}
+    cb = line.get("cpu_baseline")
+    if cb:
+        out["cpu_oracle_hvp_per_s"] = [_sig(cb["value"]), cb["cores"]]
+    return out
 
 
 def headline_config(batch: int, world: int) -> dict:

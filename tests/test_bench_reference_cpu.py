@@ -114,3 +114,32 @@ def test_kernel_source_hash_ignores_comments_only(tmp_path):
     assert bench.kernel_source_hash(str(tmp_path)) == h0
     f.write_text(text.replace("T v, d1;", "T d1, v;", 1))
     assert bench.kernel_source_hash(str(tmp_path)) != h0
+
+
+def test_compact_summary_fits_the_end_of_the_output():
+    # a line shaped like the GPU arm's, every workload row and the uneven
+    # batch included, with long unrounded numbers; the summary is printed as
+    # the line's last key and must fit in the last ~1.4 KB of output
+    sys.path.insert(0, ROOT)
+    import bench
+
+    rnd = 0.123456789123
+    roof = {"frac": 0.96912345678}
+    err = {"max": 2.512345678e-16, "requests": 100000}
+    line = {"value": 641234.56789, "e2e": {"value": 640987.654321}, "roofline": roof, "error_vs_oracle": err,
+            "fp32_comp": {"value": 32612345.6789, "e2e": {"value": 31987654.321}, "roofline": roof,
+                          "error_vs_oracle": err},
+            "workloads": {}, "cpu_baseline": {"value": 7712.3456789, "cores": 16}}
+    for name, kind, how, prec in bench.WORKLOAD_ROWS:
+        key = f"{name}/{bench.PREC_NAME[prec]}/{kind}/{how}"
+        rate = "hvp_per_s" if kind == "hvp" else "hessians_per_s"
+        line["workloads"][key] = {rate: 283456789.123 * rnd, "roofline": roof, "error_vs_oracle": err}
+    line["ragged_100k"] = {"ms_per_step": 7234.5678, "value": 13823.456, "untuned_ms_per_step": 7512.345,
+                           "error_vs_oracle": err, "cpu_baseline": {"value": 2.3456789}}
+    s = bench.compact_summary(line)
+    text = json.dumps(s)
+    assert len(text) <= 1400, len(text)
+    assert s["fp64"] == [641200.0, 0.969, 641000.0, 2.5e-16]
+    assert len([k for k in s if "/" in k]) == len(bench.WORKLOAD_ROWS)
+    assert s["ragged_100k"]["s_per_step"] == 7.23 and s["ragged_100k"]["requests_checked"] == 100000
+    assert s["cpu_oracle_hvp_per_s"] == [7710.0, 16]
