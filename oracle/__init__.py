@@ -20,7 +20,9 @@ no FMA contraction).  Two independent implementations are exposed:
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (closed-form special values, finite differences,
 symmetry, O1 == O2, the four-component rules of Sec. III-A, operation counts
-of Sec. V); none is "parity unpinned".
+of Sec. V) and ``tests/test_oracle_symbolic.py`` (the closed forms against
+symbolic derivatives of each function's formula, evaluated in 40-digit
+arithmetic); none is "parity unpinned".
 """
 from __future__ import annotations
 
