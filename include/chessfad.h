@@ -75,7 +75,7 @@ typedef struct CUstream_st *chessfad_stream_t;
 #define CHESSFAD_SUCCESS 0
 #define CHESSFAD_ERR_FUNCTION (-1)  /* unknown function id */
 #define CHESSFAD_ERR_SIZE (-2)      /* n < 1 or n > CHESSFAD_MAX_N */
-#define CHESSFAD_ERR_BATCH (-3)     /* batch < 0 */
+#define CHESSFAD_ERR_BATCH (-3)     /* batch < 0, or a batch whose launch grid would exceed 2^31 - 1 blocks */
 #define CHESSFAD_ERR_CHUNK (-4)     /* csize not in {0,1,2,4,8,16,32} */
 #define CHESSFAD_ERR_NULL (-5)      /* a required pointer is NULL */
 #define CHESSFAD_ERR_PARAMS (-6)    /* Fletcher-Powell parameters missing or ld < n */

@@ -198,6 +198,23 @@ static int fp_tile_rows(int n, int prec)
     return std::min(mt, (n + 7) / 8 * 8);
 }
 
+// A launch grid holds at most 2^31 - 1 blocks.  A batch that needs more is
+// rejected before anything is launched (the block count would otherwise be
+// truncated to 32 bits and part of the batch silently skipped).
+constexpr long long kMaxGridBlocks = 0x7fffffffLL;
+
+// batch points at pts_per_block points per block fit in one grid.
+static bool grid_fits_points(long long batch, int pts_per_block)
+{
+    return batch <= kMaxGridBlocks * (long long)pts_per_block;
+}
+
+// batch points at threads_per_point threads each, block_threads per block.
+static bool grid_fits_threads(long long batch, int threads_per_point, int block_threads)
+{
+    return batch <= kMaxGridBlocks * (long long)block_threads / threads_per_point;
+}
+
 static int launch(int fn, int n, long long batch, const chessfad_config &c, const void *x, const void *v,
                   void *out, const chessfad_fp_params *params, int prec, bool hvp, cudaStream_t stream)
 {
@@ -244,6 +261,7 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
             while (ppb > 1 && bytes(ppb) > kBudget) --ppb;
         }
         if (bytes(ppb) > kBudget) return CHESSFAD_ERR_SIZE;
+        if (!grid_fits_points(batch, ppb)) return CHESSFAD_ERR_BATCH;
         a.maxpts = ppb;
         e = sparse ? ops.sym_sparse(c.csize, hvp, a, stream) : ops.sym(c.csize, hvp, a, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
@@ -260,10 +278,12 @@ static int launch(int fn, int n, long long batch, const chessfad_config &c, cons
         int ppb = c.block_threads;
         while (ppb > 32 && bytes(ppb) > 200 * 1024) ppb -= 32;
         if (bytes(ppb) > 200 * 1024) return CHESSFAD_ERR_SIZE;
+        if (!grid_fits_points(batch, ppb)) return CHESSFAD_ERR_BATCH;
         a.maxpts = ppb;
         e = ops.point(c.csize, hvp, a, stream);
         return e == cudaSuccess ? CHESSFAD_SUCCESS : CHESSFAD_ERR_CUDA;
     }
+    if (!grid_fits_threads(batch, a.tpp, c.block_threads)) return CHESSFAD_ERR_BATCH;
     if (!f64 && n == 1) {
         // One variable: compute in FP64 (float I/O), see dispatch.h.
         a.nch = 1;

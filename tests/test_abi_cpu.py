@@ -92,6 +92,19 @@ def test_host_pipeline_argument_errors_without_gpu():
     assert lib.chessfad_hvp_host(0, 8, 0, 4, None, None, None, None, None, None, None, 0, 0, None) == 0
 
 
+def test_batch_beyond_one_launch_grid_is_rejected_without_gpu():
+    # a launch grid holds at most 2^31 - 1 blocks; a batch needing more is
+    # rejected on the host (never truncated to 32 bits), for every method
+    lib = cf.load()
+    d = ctypes.c_void_p(16)
+    big = 1 << 40
+    for n, cfg in ((512, cf.Config(16, 32, 256, cf.PLAIN, 0)), (512, cf.Config(8, 0, 0, cf.SYMMETRIC, 8)),
+                   (16, cf.Config(4, 0, 256, cf.POINT, 0))):
+        assert lib.chessfad_hvp_config(0, n, big, ctypes.byref(cfg), d, d, d, None, 0, None) == -3, cfg.as_dict()
+    one = cf.Config(1, 1, 256, cf.PLAIN, 0)  # n = 1 in compensated FP32 (the FP64-evaluated path)
+    assert lib.chessfad_hvp_config(0, 1, 1 << 45, ctypes.byref(one), d, d, d, None, 1, None) == -3
+
+
 def test_compensated_primitives_argument_errors_without_gpu():
     # every rejection happens on the host, before a launch (no device pointer
     # is ever dereferenced: the calls below launch nothing)
