@@ -156,9 +156,70 @@ def _stream(s) -> int | None:
     return s.cuda_stream
 
 
+def _require(t, name, dtype, shape=None):
+    """Check a tensor argument of the conveniences below before anything is
+    launched: a torch tensor of `shape` (when given) and `dtype`, contiguous
+    (row-major).  The C-named calls take raw addresses and cannot check any
+    of this."""
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype} for this precision, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: expected a contiguous (row-major) tensor")
+
+
+def _require_cuda(**tensors):
+    """Every given tensor lives on one CUDA device (checked after _require, so
+    a misshapen argument is named first).  None entries are skipped."""
+    first = None
+    for name, t in tensors.items():
+        if t is None:
+            continue
+        if t.device.type != "cuda" or (first is not None and t.device != first):
+            raise ValueError(f"{name}: expected a tensor on {first or 'a CUDA device'}, got {t.device}")
+        if first is None:
+            first = t.device
+
+
+def _points(x, name="x"):
+    """(batch, n) of a [batch, n] tensor."""
+    import torch
+
+    if not isinstance(x, torch.Tensor) or x.dim() != 2:
+        raise ValueError(f"{name}: expected a [batch, n] torch tensor")
+    return int(x.shape[0]), int(x.shape[1])
+
+
 def fp_params(A, B, E) -> FPParams:
-    """FPParams from device tensors (float64, A/B row-major [*, ld])."""
-    return FPParams(_addr(A), _addr(B), _addr(E), int(A.shape[1]))
+    """FPParams from device tensors: A, B float64 row-major [rows, ld] (the
+    leading n x n block is used), E float64 [>= n]."""
+    import torch
+
+    if not isinstance(A, torch.Tensor) or A.dim() != 2:
+        raise ValueError("A: expected a [rows, ld] torch tensor")
+    _require(A, "A", torch.float64)
+    _require(B, "B", torch.float64, A.shape)
+    if not isinstance(E, torch.Tensor) or E.dim() != 1:
+        raise ValueError("E: expected a 1-D torch tensor")
+    _require(E, "E", torch.float64)
+    _require_cuda(A=A, B=B, E=E)
+    p = FPParams(_addr(A), _addr(B), _addr(E), int(A.shape[1]))
+    p._extent = (int(A.shape[0]), int(A.shape[1]), int(E.numel()))  # rows, ld, entries of E
+    return p
+
+
+def _require_fp_extent(fn, n, params):
+    """The Fletcher-Powell parameters cover n variables (rows and E entries;
+    the library checks ld itself)."""
+    extent = getattr(params, "_extent", None) if params is not None else None
+    if fn == FLETCHER_POWELL and extent is not None and (extent[0] < n or extent[2] < n):
+        raise ValueError(f"Fletcher-Powell parameters hold {extent[0]} rows and {extent[2]} E entries, "
+                         f"fewer than n = {n}")
 
 
 def _check(status: int, what: str) -> int:
@@ -295,12 +356,19 @@ def _dtype(prec):
 
 
 def hvp(fn, x, v, csize=0, params=None, prec=None, stream=None, out=None, cfg=None):
-    """out = H(x_p) v_p for device tensors x, v of shape [batch, n]."""
+    """out = H(x_p) v_p for device tensors x, v of shape [batch, n] (float64
+    for FP64, float32 for FP32_COMP; prec defaults from x's dtype)."""
     import torch
 
+    batch, n = _points(x)
     if prec is None:
         prec = FP64 if x.dtype == torch.float64 else FP32_COMP
-    batch, n = x.shape
+    _require(x, "x", _dtype(prec), (batch, n))
+    _require(v, "v", _dtype(prec), (batch, n))
+    if out is not None:
+        _require(out, "out", _dtype(prec), (batch, n))
+    _require_fp_extent(fn, n, params)
+    _require_cuda(x=x, v=v, out=out)
     if out is None:
         out = torch.empty_like(x)
     if cfg is not None:
@@ -311,12 +379,18 @@ def hvp(fn, x, v, csize=0, params=None, prec=None, stream=None, out=None, cfg=No
 
 
 def hessian(fn, x, csize=0, params=None, prec=None, stream=None, out=None, cfg=None):
-    """H[p] = Hessian of f at x_p for a device tensor x of shape [batch, n]."""
+    """H[p] = Hessian of f at x_p for a device tensor x of shape [batch, n]
+    (dtypes as for hvp); out is [batch, n, n]."""
     import torch
 
+    batch, n = _points(x)
     if prec is None:
         prec = FP64 if x.dtype == torch.float64 else FP32_COMP
-    batch, n = x.shape
+    _require(x, "x", _dtype(prec), (batch, n))
+    if out is not None:
+        _require(out, "out", _dtype(prec), (batch, n, n))
+    _require_fp_extent(fn, n, params)
+    _require_cuda(x=x, out=out)
     if out is None:
         out = torch.empty((batch, n, n), dtype=x.dtype, device=x.device)
     if cfg is not None:
@@ -510,7 +584,14 @@ class UserFunction:
     def hvp(self, x, v, params=None, stream=None, out=None, cfg=None):
         import torch
 
-        batch, n = x.shape
+        batch, n = _points(x)
+        _require(x, "x", _dtype(self.prec), (batch, n))
+        _require(v, "v", _dtype(self.prec), (batch, n))
+        if out is not None:
+            _require(out, "out", _dtype(self.prec), (batch, n))
+        if params is not None:
+            _require(params, "params", torch.float64)
+        _require_cuda(x=x, v=v, out=out, params=params)
         if out is None:
             out = torch.empty_like(x)
         _check(chessfad_user_hvp_config(self.handle, n, batch, cfg, x, v, out, params, stream), "chessfad_user_hvp")
@@ -519,7 +600,13 @@ class UserFunction:
     def hessian(self, x, params=None, stream=None, out=None, cfg=None):
         import torch
 
-        batch, n = x.shape
+        batch, n = _points(x)
+        _require(x, "x", _dtype(self.prec), (batch, n))
+        if out is not None:
+            _require(out, "out", _dtype(self.prec), (batch, n, n))
+        if params is not None:
+            _require(params, "params", torch.float64)
+        _require_cuda(x=x, out=out, params=params)
         if out is None:
             out = torch.empty((batch, n, n), dtype=x.dtype, device=x.device)
         _check(chessfad_user_hessian_config(self.handle, n, batch, cfg, x, out, params, stream),
