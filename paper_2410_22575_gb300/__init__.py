@@ -507,6 +507,12 @@ class RaggedPlan:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
 
     def run(self, xpack, vpack, outpack, params=None, stream=None):
+        """H v of every request: packed x, v, out (the plan's dtype, one shape,
+        contiguous) on the workspace's CUDA device."""
+        _require(xpack, "xpack", _dtype(self.prec))
+        _require(vpack, "vpack", _dtype(self.prec), xpack.shape)
+        _require(outpack, "outpack", _dtype(self.prec), xpack.shape)
+        _require_cuda(workspace=self.workspace, xpack=xpack, vpack=vpack, outpack=outpack)
         _check(chessfad_hvp_ragged(self.handle, xpack, vpack, outpack, params, self.workspace,
                                    self.workspace.numel(), stream), "chessfad_hvp_ragged")
         return outpack

@@ -83,3 +83,16 @@ def test_user_function_conveniences_check_too():
         uf.hessian(x, out=torch.zeros(4, 6, dtype=torch.float64))
     with pytest.raises(TypeError, match="params"):
         uf.hvp(x, v, params=torch.zeros(3, dtype=torch.float32))
+
+
+def test_ragged_plan_run_checks_its_packs():
+    plan = cf.RaggedPlan.__new__(cf.RaggedPlan)  # the checks come before the plan is used
+    plan.prec, plan.handle = cf.FP32_COMP, None
+    plan.workspace = torch.zeros(256, dtype=torch.uint8)
+    x = torch.zeros(10)
+    with pytest.raises(TypeError, match="float32"):
+        plan.run(x.double(), x.double(), x.double())
+    with pytest.raises(ValueError, match="outpack: expected shape"):
+        plan.run(x, x, torch.zeros(9))
+    with pytest.raises(ValueError, match="CUDA"):
+        plan.run(x, x, x)
