@@ -143,3 +143,31 @@ def test_compact_summary_fits_the_end_of_the_output():
     assert len([k for k in s if "/" in k]) == len(bench.WORKLOAD_ROWS)
     assert s["ragged_100k"]["s_per_step"] == 7.23 and s["ragged_100k"]["requests_checked"] == 100000
     assert s["cpu_oracle_hvp_per_s"] == [7710.0, 16]
+
+
+def test_evaluation_counts_of_the_flop_model_match_the_oracles_algorithms(orc):
+    # The bench's model multiplies a per-evaluation cost by the number of
+    # evaluations of f per point: n * ceil(n/c) for the plain method (Alg. 5 /
+    # Alg. 7) and sym_items(n, c) for the symmetric one (Alg. 6 / Alg. 8).
+    # Both counts are read here off the oracle's operation counters (a call's
+    # cost is fixed by c and n) and off a brute-force enumeration of the
+    # (row, chunk) pairs, ragged last chunks included.
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    for n in (1, 5, 12, 33):
+        x = np.random.Generator(np.random.PCG64(n)).uniform(-2, 2, n)
+        for c in (1, 2, 4, 8, 16, 32):
+            nch = -(-n // c)
+            brute = sum(1 for i in range(n) for j in range(nch) if j >= i // c)
+            assert bench.sym_items(n, c) == brute, (n, c)
+            _, m_one, _ = orc.count_ops(orc.eval_hd, 0, c, orc.chunk_init(x, 0, 0, c))
+            _, m_plain, _ = orc.count_ops(orc.chunk_hess, 0, x, c)
+            _, m_sym, _ = orc.count_ops(orc.schunk_hess, 0, x, c)
+            if m_one:
+                assert m_plain == m_one * n * nch, (n, c)
+                assert m_sym == m_one * bench.sym_items(n, c), (n, c)
+            if n % c == 0:  # Sec. V: n (n/c + 1) / 2 evaluations
+                assert bench.sym_items(n, c) == n * (n // c + 1) // 2
